@@ -1,0 +1,226 @@
+/*
+ * cast.h -- C ABI of the GB300 state-vector gate engine.
+ *
+ * The engine applies a stream of k-qubit unitaries (k = 1..7) to a 2^n
+ * amplitude complex state vector held in GPU memory (Section II-A of the
+ * paper, Eq. 1-3), optionally after the paper's agglomerative, sparsity-aware
+ * gate fusion (Section IV, Algorithm 1), and computes expectation values and
+ * adjoint gradients of parametrised circuits on the same state.
+ *
+ * Conventions shared by every call
+ *   - Qubit q is bit q of the amplitude index (Eq. 1: U on qubit q is
+ *     I^(n-q-1) (x) U (x) I^q, little-endian).
+ *   - Amplitudes are interleaved (re, im): complex64 = 2 x float,
+ *     complex128 = 2 x double.  The buffer is 2^n * S bytes, S = 8 or 16.
+ *   - Gate matrices are given in complex128, row-major, interleaved, 2^k x 2^k;
+ *     bit i of a row/column index belongs to qubits[i] (caller's order).
+ *   - Every pointer argument is borrowed for the duration of the call only;
+ *     the library copies what it needs before returning.
+ *   - Work on a state is queued on the CUDA stream given when the state was
+ *     created or wrapped, and is asynchronous with respect to the host, except
+ *     for calls that return host values (copy_to_host, expectation,
+ *     adjoint_grad, fuse) which wait for their own results.
+ *   - Every call validates its arguments before any GPU work is queued and
+ *     returns a cast_status; on failure nothing has been queued and
+ *     cast_last_error() describes the problem.  No call aborts the process.
+ *
+ * Thread safety: distinct states may be used from distinct host threads;
+ * one state must not be used by two threads at once.
+ */
+#ifndef CAST_H
+#define CAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAST_MAX_QUBITS 34 /* 2^34 complex64 = 128 GiB */
+#define CAST_MAX_K 7       /* largest gate the kernels accept */
+
+typedef enum { CAST_C64 = 0, CAST_C128 = 1 } cast_dtype;
+
+typedef enum {
+    CAST_OK = 0,
+    CAST_ERR_ARG = 1,         /* invalid argument (nothing queued) */
+    CAST_ERR_OOM = 2,         /* device or pinned-host allocation failed */
+    CAST_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    CAST_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    CAST_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+} cast_status;
+
+/* Opaque state-vector handle. */
+typedef struct cast_sv cast_sv;
+
+/* ------------------------------------------------------------------------
+ * State vectors
+ * ---------------------------------------------------------------------- */
+
+/* Allocate a 2^n_qubits state of type dt on the current CUDA device, set to
+ * |0...0>, bound to `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream).  1 <= n_qubits <= CAST_MAX_QUBITS.  The library owns the memory
+ * until cast_sv_destroy.  CAST_ERR_OOM if the device allocation fails. */
+cast_status cast_sv_create(int n_qubits, cast_dtype dt, void *cuda_stream, cast_sv **out);
+
+/* Wrap caller-owned device memory (2^n_qubits amplitudes of type dt, 256-byte
+ * aligned) without copying it; the contents are used as they are.  The
+ * caller keeps ownership and must keep the memory alive until
+ * cast_sv_destroy(*out). */
+cast_status cast_sv_wrap(void *device_ptr, int n_qubits, cast_dtype dt, void *cuda_stream,
+                         cast_sv **out);
+
+/* Release the handle (and the amplitudes if the library allocated them).
+ * Waits for the state's queued work first.  NULL is accepted. */
+cast_status cast_sv_destroy(cast_sv *sv);
+
+/* Size and location of a state. Any out-pointer may be NULL. */
+cast_status cast_sv_info(const cast_sv *sv, int *n_qubits, cast_dtype *dt, void **device_ptr);
+
+/* Set the state to the computational basis state |index>, index < 2^n. */
+cast_status cast_sv_set_basis(cast_sv *sv, uint64_t index);
+
+/* Copy all 2^n amplitudes to / from host memory (2^n * S bytes, interleaved).
+ * Both wait for completion before returning. */
+cast_status cast_sv_copy_to_host(const cast_sv *sv, void *host);
+cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host);
+
+/* ------------------------------------------------------------------------
+ * Single gates (Eq. 3)
+ * ---------------------------------------------------------------------- */
+
+/* Apply one k-qubit gate, 1 <= k <= min(CAST_MAX_K, n): for every t in
+ * [0, 2^(n-k)) gather the 2^k amplitudes whose indices differ only in the
+ * target bits, multiply by the 2^k x 2^k matrix, scatter back (Eq. 3).
+ * qubits: k distinct values in [0, n).  matrix: 4^k complex128 entries.
+ * Entries with |re|, |im| <= zero_tol (1e-12) are treated as zero when the
+ * library picks a diagonal, monomial or dense kernel for the matrix. */
+cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix);
+
+/* ------------------------------------------------------------------------
+ * Circuits and gate fusion (Section IV)
+ * ---------------------------------------------------------------------- */
+
+typedef enum {
+    CAST_GATE_MATRIX = 0, /* explicit matrix in cast_gate.matrix */
+    CAST_GATE_H = 1, CAST_GATE_X = 2, CAST_GATE_Y = 3, CAST_GATE_Z = 4,
+    CAST_GATE_S = 5, CAST_GATE_T = 6,
+    CAST_GATE_RX = 7, CAST_GATE_RY = 8, CAST_GATE_RZ = 9, /* exp(-i theta P / 2) */
+    CAST_GATE_U3 = 10,   /* params (theta, phi, lambda) */
+    CAST_GATE_CX = 11, CAST_GATE_CZ = 12,
+    CAST_GATE_CP = 13,   /* diag(1, 1, 1, e^{i phi}) */
+    CAST_GATE_SWAP = 14
+} cast_gate_kind;
+
+/* One gate.  For CX / CZ / CP qubits[0] is the control.  A rotation (RX, RY,
+ * RZ, CP) with param_index >= 0 takes its angle from the params array given
+ * to the call instead of params[0]. */
+typedef struct {
+    int32_t kind;          /* cast_gate_kind */
+    int32_t k;             /* number of qubits (1..CAST_MAX_K) */
+    int32_t qubits[CAST_MAX_K];
+    int32_t param_index;   /* -1 = fixed angles in params[] */
+    double params[3];
+    const double *matrix;  /* CAST_GATE_MATRIX only: 4^k complex128 */
+} cast_gate;
+
+/* n_params: length of the angle array passed with the circuit; every
+ * param_index must be below it.  Only RX, RY, RZ and CP may be parametrised. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    const cast_gate *gates;
+    int32_t n_params;
+} cast_circuit;
+
+typedef enum {
+    CAST_FUSE_NONE = 0,     /* apply the gates as given */
+    CAST_FUSE_SIZE = 1,     /* fuse while the fused block has <= max_k qubits */
+    CAST_FUSE_ADAPTIVE = 2  /* size test plus the cost-model test (Section IV-C) */
+} cast_fusion_mode;
+
+typedef struct {
+    int32_t fusion;        /* cast_fusion_mode, default CAST_FUSE_ADAPTIVE */
+    int32_t max_k;         /* largest fused gate, 1..CAST_MAX_K, default 5 */
+    int32_t agglomerative; /* 1: raise the allowed size 2..max_k (Section IV-B), default 1 */
+    int32_t op_cap;        /* adaptive: largest operation count of a fused gate, default 4096 */
+    double zero_tol;       /* |real scalar| <= zero_tol counts as zero, default 1e-12 */
+    int32_t amp_ops_per_pass; /* adaptive cost model: operations per amplitude that take as
+                                 long as one pass over the state; 0 = measured default for
+                                 the state type (complex64: 82, complex128: 2) */
+} cast_options;
+
+/* Fill *o with the defaults listed above. */
+void cast_options_default(cast_options *o);
+
+/* Apply a whole circuit: fuse on the host (unless opt->fusion is NONE),
+ * classify each resulting gate, upload all matrices once, and queue one
+ * kernel per gate.  params: angles for gates with param_index >= 0 (may be
+ * NULL if there are none).  opt NULL = defaults.
+ * c->n_qubits must equal the state's qubit count. */
+cast_status cast_apply_circuit(cast_sv *sv, const cast_circuit *c, const double *params,
+                               const cast_options *opt);
+
+/* Host only (no GPU work): run the fusion pass and report its output.
+ * On entry *n_out is the capacity of the output arrays (in gates); on return
+ * it is the number of fused gates.  ks_out[g]: size of fused gate g;
+ * qubits_out: CAST_MAX_K entries per gate, sorted ascending, unused = -1;
+ * opcount_out[g]: operation count (Section IV-C: 2 per non-zero real scalar);
+ * matrices_out (may be NULL): 4^CAST_MAX_K complex128 entries per gate, each
+ * gate's 2^k x 2^k matrix stored row-major at the start of its slot, local
+ * bit i <-> qubits_out[g*CAST_MAX_K + i].  CAST_ERR_ARG if the capacity is
+ * too small (then *n_out is the required count).  With amp_ops_per_pass = 0
+ * the complex64 default is used. */
+cast_status cast_fuse(const cast_circuit *c, const double *params, const cast_options *opt,
+                      int *n_out, int *ks_out, int *qubits_out, int64_t *opcount_out,
+                      double *matrices_out);
+
+/* Host only: operation count of a 2^k x 2^k complex128 matrix, i.e. 2 x the
+ * number of real scalars with magnitude > zero_tol (Section IV-C). */
+int64_t cast_opcount(const double *matrix, int k, double zero_tol);
+
+/* ------------------------------------------------------------------------
+ * Observables and gradients
+ * ---------------------------------------------------------------------- */
+
+/* A sum of Pauli strings, each c_t * P_t with P_t given by two bit masks:
+ * bit q of x_mask set = X or Y on qubit q; bit q of z_mask set = Z or Y on
+ * qubit q (both set = Y).  Coefficients are real, so H is Hermitian. */
+typedef struct {
+    int32_t n_terms;
+    const double *coeffs;
+    const uint64_t *x_masks;
+    const uint64_t *z_masks;
+} cast_pauli_sum;
+
+/* *out = <psi|H|psi> accumulated in FP64.  Waits for the result. */
+cast_status cast_expectation(const cast_sv *sv, const cast_pauli_sum *h, double *out);
+
+/* Adjoint differentiation of E(theta) = <psi0|U(theta)^dag H U(theta)|psi0>
+ * for a circuit whose parametrised gates are RX/RY/RZ (exp(-i theta P / 2))
+ * with param_index >= 0; fixed gates may be of any kind.
+ *   psi   : on entry the initial state psi0; on return psi0 recomputed by
+ *           uncomputation (equal to the input up to rounding)
+ *   lam   : work state of the same size and type (contents ignored); its
+ *           stream waits for psi's stream around the call
+ *   params: the circuit's c->n_params angles; grad_out[p] for
+ *           p < c->n_params receives dE/dtheta_p; energy_out receives E.
+ * Uses two state vectors in total, independent of the circuit depth:
+ * the forward pass, lam = H psi, then one backward sweep that applies
+ * U_j^dag to psi and lam and, at each rotation, forms Im<lam|P|psi> (the
+ * derivative of exp(-i theta P / 2)) with FP64-class accumulation.
+ * Waits for the result. */
+cast_status cast_adjoint_grad(cast_sv *psi, cast_sv *lam, const cast_circuit *c, const double *params,
+                              const cast_pauli_sum *h, double *energy_out, double *grad_out);
+
+/* Thread-local description of the last failure on this host thread. */
+const char *cast_last_error(void);
+
+/* Version string of this build. */
+const char *cast_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAST_H */

@@ -1,0 +1,104 @@
+// Adjoint differentiation step for a rotation U = exp(-i theta P / 2) on one
+// qubit (P in {X, Y, Z}).
+//
+// With psi_j the state after gate j and lam_j = U_{j+1}^dag ... U_G^dag H psi_G,
+//   dE/dtheta_j = 2 Re <lam_j| dU_j/dtheta psi_{j-1}> = Im <lam_j| P |psi_j>,
+// because dU/dtheta = (-i/2) P U.  One pass over the amplitude pairs
+// (x, x + 2^q) reads psi and lam, accumulates Im(conj(lam) . P psi) with an
+// FP64-class accumulator, and writes back U^dag psi and U^dag lam, where
+// U^dag = cos(theta/2) I + i sin(theta/2) P.  Each block leaves one partial
+// sum; they are reduced in a fixed order afterwards.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace cast {
+namespace {
+
+// (P v)_0, (P v)_1 for P = X (1), Y (2), Z (3)
+template <typename T2>
+__device__ __forceinline__ void pauli_pair(int pauli, T2 v0, T2 v1, T2 &o0, T2 &o1) {
+    if (pauli == 1) {
+        o0 = v1;
+        o1 = v0;
+    } else if (pauli == 2) {  // Y|0> = i|1>, Y|1> = -i|0>
+        o0.x = v1.y;
+        o0.y = -v1.x;  // -i v1
+        o1.x = -v0.y;
+        o1.y = v0.x;   // i v0
+    } else {
+        o0 = v0;
+        o1.x = -v1.x;
+        o1.y = -v1.y;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_adj_rot(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam, uint64_t npairs,
+          int q, int pauli, R c, R s, double *__restrict__ partials) {
+    using T2 = typename Cx<R>::T;
+    Acc<R> acc;
+    const uint64_t bit = uint64_t(1) << q;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < npairs; t += stride) {
+        const uint64_t i0 = ((t >> q) << (q + 1)) | (t & (bit - 1));
+        const uint64_t i1 = i0 | bit;
+        const T2 p0 = psi[i0], p1 = psi[i1], l0 = lam[i0], l1 = lam[i1];
+        T2 pp0, pp1, pl0, pl1;
+        pauli_pair(pauli, p0, p1, pp0, pp1);
+        pauli_pair(pauli, l0, l1, pl0, pl1);
+        // Im(conj(l) * pp) = l.x * pp.y - l.y * pp.x
+        acc.add(l0.x * pp0.y - l0.y * pp0.x);
+        acc.add(l1.x * pp1.y - l1.y * pp1.x);
+        // U^dag v = c v + i s (P v)
+        T2 o;
+        o.x = c * p0.x - s * pp0.y; o.y = c * p0.y + s * pp0.x; psi[i0] = o;
+        o.x = c * p1.x - s * pp1.y; o.y = c * p1.y + s * pp1.x; psi[i1] = o;
+        o.x = c * l0.x - s * pl0.y; o.y = c * l0.y + s * pl0.x; lam[i0] = o;
+        o.x = c * l1.x - s * pl1.y; o.y = c * l1.y + s * pl1.x; lam[i1] = o;
+    }
+    const double v = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+// grad[p] = sum of the gate values whose parameter index is p, in gate order
+__global__ void k_param_sum(const double *__restrict__ gate_vals, const int *__restrict__ gate_pidx,
+                            int ngates, double *__restrict__ grad, int nparams) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparams) return;
+    double s = 0.0;
+    for (int g = 0; g < ngates; g++)
+        if (gate_pidx[g] == p) s += gate_vals[g];
+    grad[p] = s;
+}
+
+}  // namespace
+
+cast_status launch_adjoint_rotation(cast_sv *psi, cast_sv *lam, int q, int pauli, double theta,
+                                    double *d_partials) {
+    const uint64_t npairs = uint64_t(1) << (psi->n - 1);
+    const int G = reduce_grid_blocks();
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    if (psi->dt == CAST_C64)
+        k_adj_rot<float><<<G, 256, 0, psi->stream>>>(reinterpret_cast<float2 *>(psi->data),
+                                                      reinterpret_cast<float2 *>(lam->data), npairs, q,
+                                                      pauli, (float)c, (float)s, d_partials);
+    else
+        k_adj_rot<double><<<G, 256, 0, psi->stream>>>(reinterpret_cast<double2 *>(psi->data),
+                                                       reinterpret_cast<double2 *>(lam->data), npairs, q,
+                                                       pauli, c, s, d_partials);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+cast_status launch_param_sum(cudaStream_t st, const double *gate_vals, const int *gate_pidx, int ngates,
+                             double *grad, int nparams) {
+    if (nparams <= 0) return CAST_OK;
+    k_param_sum<<<(nparams + 127) / 128, 128, 0, st>>>(gate_vals, gate_pidx, ngates, grad, nparams);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+}  // namespace cast

@@ -1,0 +1,322 @@
+// Gate-application kernels for sm_103a (Eq. 3 of the paper: 2^(n-k)
+// gathered 2^k x 2^k matrix-vector products on a 2^n state).
+//
+// Kernel families (the host picks one per prepared gate):
+//   k_dense<R,K>       K <= 5, any targets.  One slice (2^K amplitudes) per
+//                      thread iteration, kept in registers.  The matrix travels
+//                      in the launch's parameter space (<= 16 KB) so every
+//                      thread reads the same entry from the constant bank in
+//                      lockstep (broadcast).
+//   k_dense_tile<R,K>  K = 6, 7.  A CTA stages 2^K x TS amplitudes in shared
+//                      memory, then each thread forms (row, slice) outputs
+//                      reading the matrix from global memory (L1-resident).
+//   k_diag<R,K>        diagonal gates: one pass over the amplitudes, each
+//                      multiplied by d[local index]; entries equal to 1 are
+//                      neither read nor written.
+//   k_mono<R,K>        monomial gates (one non-zero per row and column:
+//                      X, CX, SWAP, Y, ...): gather the source of every row,
+//                      multiply by its phase, scatter; fixed points with phase
+//                      1 are skipped.
+//
+// Slice enumeration follows Eq. 4: the base index of slice t is t with a zero
+// bit inserted at every target position (targets sorted ascending); member j
+// of the slice adds 2^q[i] for every set bit i of j.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace cast {
+namespace {
+
+// ------------------------------------------------------------ dense, K <= 5
+template <typename R, int K>
+struct DenseMat {
+    typename Cx<R>::T m[1 << K][1 << K];
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256)
+k_dense(typename Cx<R>::T *__restrict__ sv, uint64_t nslices, Targets tg,
+        const __grid_constant__ DenseMat<R, K> U) {
+    using T2 = typename Cx<R>::T;
+    constexpr int D = 1 << K;
+    uint64_t p[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nslices; t += stride) {
+        const uint64_t base = slice_base<K>(t, tg);
+        T2 x[D];
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            uint64_t off = 0;
+#pragma unroll
+            for (int i = 0; i < K; i++)
+                if ((j >> i) & 1) off += p[i];
+            x[j] = sv[base + off];
+        }
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const T2 u = U.m[r][c];
+                re = fma(u.x, x[c].x, re);
+                re = fma(-u.y, x[c].y, re);
+                im = fma(u.x, x[c].y, im);
+                im = fma(u.y, x[c].x, im);
+            }
+            uint64_t off = 0;
+#pragma unroll
+            for (int i = 0; i < K; i++)
+                if ((r >> i) & 1) off += p[i];
+            T2 y;
+            y.x = re;
+            y.y = im;
+            sv[base + off] = y;
+        }
+    }
+}
+
+// --------------------------------------------------------- dense, K = 6, 7
+template <typename R, int K, int TS>
+__global__ void __launch_bounds__(256)
+k_dense_tile(typename Cx<R>::T *__restrict__ sv, uint64_t nslices, Targets tg,
+             const typename Cx<R>::T *__restrict__ U) {
+    using T2 = typename Cx<R>::T;
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *X = reinterpret_cast<T2 *>(smem_raw);  // [D][TS]
+    const uint64_t ntiles = (nslices + TS - 1) / TS;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t t0 = tile * TS;
+        for (int idx = threadIdx.x; idx < D * TS; idx += blockDim.x) {
+            const int j = idx / TS, s = idx % TS;
+            const uint64_t t = t0 + s;
+            if (t < nslices) X[idx] = sv[slice_base<K>(t, tg) + member_offset<K>(j, tg)];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < D * TS; idx += blockDim.x) {
+            const int r = idx / TS, s = idx % TS;
+            const uint64_t t = t0 + s;
+            if (t >= nslices) continue;
+            R re = 0, im = 0;
+            const T2 *urow = U + size_t(r) * D;
+#pragma unroll 8
+            for (int c = 0; c < D; c++) {
+                const T2 u = __ldg(urow + c);
+                const T2 xv = X[c * TS + s];
+                re = fma(u.x, xv.x, re);
+                re = fma(-u.y, xv.y, re);
+                im = fma(u.x, xv.y, im);
+                im = fma(u.y, xv.x, im);
+            }
+            T2 y;
+            y.x = re;
+            y.y = im;
+            sv[slice_base<K>(t, tg) + member_offset<K>(r, tg)] = y;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- diagonal
+template <typename R, int K>
+struct DiagVec {
+    typename Cx<R>::T d[1 << K];
+    uint32_t skip;  // bit j set: d[j] == 1, amplitudes with local index j untouched
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256)
+k_diag(typename Cx<R>::T *__restrict__ sv, uint64_t N, Targets tg,
+       const __grid_constant__ DiagVec<R, K> D) {
+    using T2 = typename Cx<R>::T;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        int j = 0;
+#pragma unroll
+        for (int b = 0; b < K; b++) j |= int((i >> tg.q[b]) & 1) << b;
+        if ((K <= 5) && ((D.skip >> j) & 1)) continue;
+        sv[i] = cmul(D.d[j], sv[i]);
+    }
+}
+
+// ---------------------------------------------------------------- monomial
+template <typename R, int K>
+struct MonoVec {
+    typename Cx<R>::T ph[1 << K];
+    uint8_t perm[1 << K];
+    int unit;  // all phases are exactly 1
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256)
+k_mono(typename Cx<R>::T *__restrict__ sv, uint64_t nslices, Targets tg,
+       const __grid_constant__ MonoVec<R, K> M) {
+    using T2 = typename Cx<R>::T;
+    constexpr int D = 1 << K;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nslices; t += stride) {
+        const uint64_t base = slice_base<K>(t, tg);
+        T2 v[D];
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            const int c = M.perm[r];
+            if (c != r || !M.unit) v[r] = sv[base + member_offset<K>(c, tg)];
+        }
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            const int c = M.perm[r];
+            if (c == r && M.unit) continue;
+            sv[base + member_offset<K>(r, tg)] = M.unit ? v[r] : cmul(M.ph[r], v[r]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ launch glue
+uint64_t grid_for(uint64_t work_items, int per_sm) {
+    uint64_t cap = uint64_t(sm_count_cached()) * per_sm;
+    uint64_t need = (work_items + 255) / 256;
+    if (need < 1) need = 1;
+    return need < cap ? need : cap;
+}
+
+template <typename R>
+typename Cx<R>::T to_dev(cplx z) {
+    typename Cx<R>::T v;
+    v.x = (R)z.real();
+    v.y = (R)z.imag();
+    return v;
+}
+
+template <typename R, int K>
+cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
+    using T2 = typename Cx<R>::T;
+    const uint64_t ns = uint64_t(1) << (sv->n - K);
+    if constexpr (K <= 5) {
+        DenseMat<R, K> U;
+        for (int r = 0; r < (1 << K); r++)
+            for (int c = 0; c < (1 << K); c++) U.m[r][c] = to_dev<R>(g.m[size_t(r) * (1 << K) + c]);
+        const int per_sm = K <= 3 ? 8 : (K == 4 ? 4 : 2);
+        k_dense<R, K><<<(unsigned)grid_for(ns, per_sm), 256, 0, sv->stream>>>(
+            reinterpret_cast<T2 *>(sv->data), ns, tg, U);
+    } else {
+        constexpr int TS = 32;
+        const size_t mat_bytes = sizeof(T2) << (2 * K);
+        if (sv->matrices.bytes < mat_bytes) return fail(CAST_ERR_ARG, "matrix buffer too small");
+        // stage the converted matrix through pinned memory, then to the device
+        T2 *h = reinterpret_cast<T2 *>(sv->host_pinned);
+        CAST_CUDA(cudaStreamSynchronize(sv->stream));  // previous users of the staging buffer
+        for (size_t i = 0; i < (size_t(1) << (2 * K)); i++) h[i] = to_dev<R>(g.m[i]);
+        CAST_CUDA(cudaMemcpyAsync(sv->matrices.ptr, h, mat_bytes, cudaMemcpyHostToDevice, sv->stream));
+        const size_t smem = sizeof(T2) * (1 << K) * TS;
+        CAST_CUDA(cudaFuncSetAttribute(k_dense_tile<R, K, TS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const uint64_t ntiles = (ns + TS - 1) / TS;
+        const uint64_t grid = ntiles < uint64_t(sm_count_cached()) * 4 ? ntiles : uint64_t(sm_count_cached()) * 4;
+        k_dense_tile<R, K, TS><<<(unsigned)grid, 256, smem, sv->stream>>>(
+            reinterpret_cast<T2 *>(sv->data), ns, tg, reinterpret_cast<const T2 *>(sv->matrices.ptr));
+    }
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+template <typename R, int K>
+cast_status run_diag(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
+    using T2 = typename Cx<R>::T;
+    DiagVec<R, K> D;
+    D.skip = 0;
+    for (int j = 0; j < (1 << K); j++) {
+        D.d[j] = to_dev<R>(g.diag[j]);
+        if (K <= 5 && g.diag[j] == cplx(1.0, 0.0)) D.skip |= 1u << j;
+    }
+    const uint64_t N = uint64_t(1) << sv->n;
+    k_diag<R, K><<<(unsigned)grid_for(N, 8), 256, 0, sv->stream>>>(
+        reinterpret_cast<T2 *>(sv->data), N, tg, D);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+template <typename R, int K>
+cast_status run_mono(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
+    using T2 = typename Cx<R>::T;
+    MonoVec<R, K> M;
+    M.unit = g.unit_phases ? 1 : 0;
+    for (int j = 0; j < (1 << K); j++) {
+        M.ph[j] = to_dev<R>(g.phase[j]);
+        M.perm[j] = (uint8_t)g.perm[j];
+    }
+    const uint64_t ns = uint64_t(1) << (sv->n - K);
+    k_mono<R, K><<<(unsigned)grid_for(ns, 8), 256, 0, sv->stream>>>(
+        reinterpret_cast<T2 *>(sv->data), ns, tg, M);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+template <typename R, int K>
+cast_status dispatch_k(cast_sv *sv, const PreparedGate &g) {
+    Targets tg;
+    for (int i = 0; i < CAST_MAX_K; i++) tg.q[i] = i < g.k ? g.q[i] : 0;
+    switch (g.cls) {
+        case CLS_IDENTITY: return CAST_OK;
+        case CLS_DIAG: return run_diag<R, K>(sv, g, tg);
+        case CLS_MONO: return run_mono<R, K>(sv, g, tg);
+        default: return run_dense<R, K>(sv, g, tg);
+    }
+}
+
+template <typename R>
+cast_status dispatch(cast_sv *sv, const PreparedGate &g) {
+    switch (g.k) {
+        case 1: return dispatch_k<R, 1>(sv, g);
+        case 2: return dispatch_k<R, 2>(sv, g);
+        case 3: return dispatch_k<R, 3>(sv, g);
+        case 4: return dispatch_k<R, 4>(sv, g);
+        case 5: return dispatch_k<R, 5>(sv, g);
+        case 6: return dispatch_k<R, 6>(sv, g);
+        case 7: return dispatch_k<R, 7>(sv, g);
+        default: return fail(CAST_ERR_ARG, "gate size out of range");
+    }
+}
+
+__global__ void k_set_one(void *data, int dt, uint64_t index) {
+    if (dt == CAST_C64)
+        reinterpret_cast<float2 *>(data)[index] = make_float2(1.f, 0.f);
+    else
+        reinterpret_cast<double2 *>(data)[index] = make_double2(1.0, 0.0);
+}
+
+}  // namespace
+
+cast_status launch_set_one(cast_sv *sv, uint64_t index) {
+    k_set_one<<<1, 1, 0, sv->stream>>>(sv->data, sv->dt, index);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+int sm_count_cached() {
+    static std::mutex mu;
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (sms[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = v > 0 ? v : 1;
+    }
+    return sms[dev];
+}
+
+cast_status launch_gate(cast_sv *sv, const PreparedGate &g) {
+    if (sv->dt == CAST_C64) return dispatch<float>(sv, g);
+    return dispatch<double>(sv, g);
+}
+
+}  // namespace cast

@@ -1,0 +1,121 @@
+// Internal declarations shared by the host side (capi.cpp, fusion.cpp,
+// gates.cpp) and the CUDA kernels (apply.cu, reduce.cu, adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cast.h"
+
+namespace cast {
+
+using cplx = std::complex<double>;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+cast_status fail(cast_status st, const std::string &msg);
+cast_status cuda_fail(cudaError_t e, const char *what);
+#define CAST_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------------ state handle
+struct DeviceScratch {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace cast
+
+struct cast_sv {
+    void *data = nullptr;    // 2^n amplitudes
+    int n = 0;
+    cast_dtype dt = CAST_C128;
+    cudaStream_t stream = nullptr;
+    bool owned = false;
+    int device = 0;
+    // per-state device scratch: FP64 partial sums of reductions
+    cast::DeviceScratch partials;
+    // per-state device buffer for matrices of large gates (k >= 6)
+    cast::DeviceScratch matrices;
+    // pinned host staging for results and matrix uploads
+    void *host_pinned = nullptr;
+    size_t host_pinned_bytes = 0;
+};
+
+namespace cast {
+
+inline size_t amp_bytes(cast_dtype dt) { return dt == CAST_C128 ? 16 : 8; }
+
+// ---------------------------------------------------------- prepared gates
+enum GateClass { CLS_IDENTITY = 0, CLS_DIAG = 1, CLS_MONO = 2, CLS_DENSE = 3 };
+
+// A gate ready for a kernel: qubits sorted ascending, matrix permuted to that
+// order, entries below the zero tolerance set to exactly zero.
+struct PreparedGate {
+    int k = 0;
+    int q[CAST_MAX_K] = {0};
+    int cls = CLS_DENSE;
+    std::vector<cplx> m;        // 4^k, row-major, sorted-qubit order
+    std::vector<cplx> diag;     // CLS_DIAG: 2^k diagonal entries
+    std::vector<int> perm;      // CLS_MONO: row r reads column perm[r]
+    std::vector<cplx> phase;    // CLS_MONO: value of the non-zero in row r
+    bool unit_phases = false;   // CLS_MONO: every phase is exactly 1
+};
+
+// Validate + sort + classify.  Returns CAST_OK or CAST_ERR_ARG.
+cast_status prepare_gate(int n, const int *qubits, int k, const cplx *matrix, double zero_tol,
+                         PreparedGate *out);
+int64_t opcount(const cplx *m, int k, double zero_tol);
+
+// Matrix of a table gate (kind != MATRIX) with the given angles.
+cast_status gate_table_matrix(int kind, int k, const double *params, std::vector<cplx> *out);
+int gate_table_arity(int kind);
+// Matrix of any cast_gate (table gate, parametrised rotation or explicit).
+cast_status gate_matrix_of(const cast_gate &g, const double *params, int n_params,
+                           std::vector<cplx> *out);
+int64_t default_amp_ops_per_pass(cast_dtype dt);
+
+// ------------------------------------------------------------ fusion pass
+struct FusedGate {
+    int k;
+    int q[CAST_MAX_K];         // sorted ascending
+    std::vector<cplx> m;       // 4^k row-major over q
+    int64_t ops;
+};
+cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast_options *opt,
+                         std::vector<FusedGate> *out);
+
+// --------------------------------------------------------------- kernels
+// Queue one prepared gate on sv's stream.
+cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
+// Queue sum_t coeff_t <psi|P_t|psi> terms sharing one x_mask; partial sums
+// of FP64 go to sv->partials; returns the number of partials written.
+cast_status launch_pauli_group(const cast_sv *sv, uint64_t x_mask, int n_terms,
+                               const double *coeffs, const uint64_t *z_masks, double *d_out,
+                               int *n_partials);
+int reduce_grid_blocks();
+int sm_count_cached();
+cast_status launch_set_one(cast_sv *sv, uint64_t index);
+cast_status launch_param_sum(cudaStream_t st, const double *gate_vals, const int *gate_pidx, int ngates,
+                             double *grad, int nparams);
+cast_status launch_finalize(cudaStream_t st, const double *d_partials, int per_slot, int nslots,
+                            double *d_out);
+cast_status launch_inner(const cast_sv *a, const cast_sv *b, double *d_partials_re,
+                         double *d_partials_im);
+// out = (or +=) sum over terms sharing x_mask of c_t P_t psi
+cast_status launch_pauli_apply(const cast_sv *psi, cast_sv *out, uint64_t x_mask, int n_terms,
+                               const double *coeffs, const uint64_t *z_masks, bool accumulate);
+// Adjoint step for a rotation exp(-i theta P / 2) on qubit q (P = 1:X, 2:Y, 3:Z):
+// partial sums of Im<lam|P_q|psi> into d_partials (reduce_grid_blocks() values),
+// then psi <- U^dag psi and lam <- U^dag lam.
+cast_status launch_adjoint_rotation(cast_sv *psi, cast_sv *lam, int q, int pauli, double theta,
+                                    double *d_partials);
+
+}  // namespace cast
