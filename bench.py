@@ -1,0 +1,328 @@
+"""Benchmark: fused-gate throughput of the state-vector engine on one GB300.
+
+Workload (one step): a 30-qubit state set to a seeded basis state |x>, then the
+30-qubit QFT and a 30-qubit random layered circuit (30 layers of
+{H, X, RX, RY, RZ} on every qubit plus CX on a random matching), both fused by
+the adaptive agglomerative fusion into gates of at most 5 qubits, then <Z_0>.
+
+  value   fused-gate GB/s: (fused gates x 2 x 2^n x bytes per amplitude)
+          / device time, state resident in HBM (8 GiB complex64 / 16 GiB
+          complex128: larger than L2, so no flush is needed between steps)
+  e2e     the same metric through the public C ABI per step: the initial state
+          copied from pinned host memory, cast_apply_circuit on both circuits
+          (host fusion included) and the <Z_0> scalar read back
+  roofline  the dominant kernel family, timed live with CUDA events on its
+          launch stream during the timed steps
+  cpu_baseline  the oracle (plain FP64 C, OpenMP) on the host cores, applying
+          the unfused QFT gates to the same 30-qubit state for a bounded time
+
+--impl reference times the oracle alone, as it stands, on the same workload.
+Multi-GPU (torchrun): replicas, one state per GPU, no collective on the data
+path; value sums all ranks' bytes over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "30q fused-gate GB/s (% of HBM roofline); VQA grads/s adjoint+batched vs plain"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="cast", choices=["cast", "reference"])
+    p.add_argument("--n", type=int, default=30)
+    p.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    p.add_argument("--max-k", type=int, default=5)
+    p.add_argument("--layers", type=int, default=30)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return mp, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_name(a):
+    return f"QFT-{a.n} + RQC-{a.n} ({a.layers} layers), adaptive fusion k<={a.max_k}"
+
+
+def workload(n, layers, seed=1):
+    x = W.random_basis_index(n, seed)
+    return x, W.qft_circuit(n), W.random_circuit(n, layers, seed)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons, every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_traffic(family):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source it was taken on is unchanged (same hash), else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2503_19894_gb300", "csrc", "apply.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(TRAFFIC_FILE):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == family and parts[1] == h and not line.startswith("#"):
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+def roofline(profile, mp, src, launches_per_step_kind="sustained"):
+    top = profile[0]
+    per_launch_bytes = top["bytes"] / top["launches"]
+    per_launch_flops = top["flops"] / top["launches"]
+    avg_s = top["ms"] / top["launches"] / 1e3
+    gbs = per_launch_bytes / avg_s / 1e9
+    # arithmetic intensity against the ridge of the unit that does the work
+    sm_mhz = mp.get("sm_max_mhz", 2070.0)
+    fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp64_tflops = 1.01  # measured FFMA64 rate on this GB300
+    alu_peak = fp64_tflops if top["name"].endswith("c128") else fp32_tflops
+    alu_t = per_launch_flops / alu_peak / 1e12
+    mem_t = per_launch_bytes / (mp["hbm_gbs"] * 1e9)
+    if alu_t > mem_t:
+        ach = per_launch_flops / avg_s / 1e12
+        r = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+             "frac": round(ach / alu_peak, 4), "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x "
+             f"{sm_mhz:.0f} MHz" if alu_peak == fp32_tflops else "measured FP64 FMA rate"}
+    else:
+        r = {"bound": "hbm", "achieved": round(gbs, 1), "peak": mp["hbm_gbs"], "unit": "GB/s",
+             "frac": round(gbs / mp["hbm_gbs"], 4), "peak_source": f"{src} hbm_gbs"}
+    r.update({"kernel": top["name"], "launches": top["launches"], "avg_ms": round(top["ms"] / top["launches"], 4),
+              "bytes_per_launch": per_launch_bytes, "hbm_gbs_achieved": round(gbs, 1),
+              "traffic": read_traffic(top["name"])})
+    return r
+
+
+def cpu_baseline(n, qft, seconds):
+    """Oracle (as it stands) on the host cores: unfused QFT gates on the
+    n-qubit complex128 state until `seconds` have passed."""
+    import oracle
+    psi = oracle.basis_state(n, 1)
+    done, t0 = 0, time.perf_counter()
+    for g in qft:
+        oracle.apply_gate(psi, g.qubits, oracle.gate_matrix(g))
+        done += 1
+        if time.perf_counter() - t0 > seconds and done >= 2:
+            break
+    dt = time.perf_counter() - t0
+    gbs = done * 2.0 * (1 << n) * 16 / dt / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {done} unfused QFT-{n} gates on a {n}-qubit complex128 state "
+                      f"({dt:.1f} s); gate-pass bytes 2 x 2^{n} x 16 per gate"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    x, qft, _ = workload(a.n, a.layers)
+    per = max(2.0, 150.0 / max(1, a.steps + a.warmup))
+    for _ in range(a.warmup):
+        cpu_baseline(a.n, qft, per)
+    t0 = time.perf_counter()
+    vals = [cpu_baseline(a.n, qft, per) for _ in range(a.steps)]
+    dt = time.perf_counter() - t0
+    v = statistics.mean(r["value"] for r in vals)
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "impl": "reference", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(a), "n_qubits": a.n,
+                                            "sample": "oracle applies the unfused QFT gates for a bounded time"},
+            "cpu_baseline": dict(vals[0], value=v),
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2503_19894_gb300 as pkg
+    from paper_2503_19894_gb300 import capi
+    capi.load()
+    mp, src = peaks()
+    n, S = a.n, (8 if a.dtype == "c64" else 16)
+    x, qft, rqc = workload(n, a.layers)
+    opts = capi.options("adaptive", a.max_k)
+    plan_q = capi.cast_plan_create(n, qft, opts=opts, dtype=a.dtype)
+    plan_r = capi.cast_plan_create(n, rqc, opts=opts, dtype=a.dtype)
+    gq, _ = capi.cast_plan_info(plan_q)
+    gr, _ = capi.cast_plan_info(plan_r)
+    fused_gates = gq + gr
+    step_bytes = fused_gates * 2.0 * (1 << n) * S
+    z0 = W.z0_observable()
+    stream = torch.cuda.current_stream()
+    sv = pkg.StateVector(n, a.dtype, init_index=x)
+
+    def step():
+        capi.cast_sv_set_basis(sv.handle, x)
+        capi.cast_plan_apply(sv.handle, plan_q)
+        capi.cast_plan_apply(sv.handle, plan_r)
+        return capi.cast_expectation(sv.handle, z0)
+
+    for _ in range(a.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        capi.cast_profile_begin()
+        e0.record(stream)
+        for _ in range(a.steps):
+            zval = step()
+        e1.record(stream)
+        barrier()
+        prof = capi.cast_profile_end()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = step_bytes * a.steps * world / (ms_max / 1e3) / 1e9
+    launches = sum(p["launches"] for p in prof)
+
+    e2e = None
+    if not a.no_e2e:
+        host = torch.zeros(1 << n, dtype=torch.complex64 if S == 8 else torch.complex128, pin_memory=True)
+        host[x] = 1
+        hv = host.numpy()
+
+        def e2e_step():
+            capi.cast_sv_copy_from_host(sv.handle, hv)
+            capi.cast_apply_circuit(sv.handle, n, qft, None, opts)
+            capi.cast_apply_circuit(sv.handle, n, rqc, None, opts)
+            return capi.cast_expectation(sv.handle, z0)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        barrier()
+        et = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(step_bytes * a.steps * world / float(et.item()) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": 8,
+               "ms_per_step": round(float(et.item()) / a.steps * 1e3, 2)}
+        del host
+    sv.close()
+    capi.cast_plan_destroy(plan_q)
+    capi.cast_plan_destroy(plan_r)
+
+    if rank == 0:
+        rf = roofline(prof, mp, src)
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
+                "config": {"workload": workload_name(a),
+                           "n_qubits": n, "state": "complex64" if S == 8 else "complex128",
+                           "fused_gates": {"qft": gq, "rqc": gr}, "l2": "state larger than L2, no flush",
+                           "parallelism": f"replicas x{world}"},
+                "hbm_frac": round(value / mp["hbm_gbs"], 4), "hbm_frac_of": src,
+                "hbm_frac_nominal_8tbs": round(value / 8000.0, 4),
+                "z0": zval, "gpu_launches": launches, "roofline": rf, "e2e": e2e,
+                "clocks": clk.summary(),
+                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in p.items()}
+                            for p in prof[:8]]}
+        if world == 1 and not a.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(n, qft, a.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

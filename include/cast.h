@@ -181,6 +181,51 @@ cast_status cast_fuse(const cast_circuit *c, const double *params, const cast_op
 int64_t cast_opcount(const double *matrix, int k, double zero_tol);
 
 /* ------------------------------------------------------------------------
+ * Plans: a circuit fused and prepared once, applied many times
+ * ---------------------------------------------------------------------- */
+
+typedef struct cast_plan cast_plan;
+
+/* Fuse (per *opt, NULL = defaults) and classify the circuit's gates on the
+ * host and keep the result.  dt selects the cost-model default when
+ * opt->amp_ops_per_pass is 0.  No GPU work.  The plan can be applied to any
+ * state with c->n_qubits qubits, of either type. */
+cast_status cast_plan_create(const cast_circuit *c, const double *params, const cast_options *opt,
+                             cast_dtype dt, cast_plan **out);
+
+/* Queue the plan's gates on the state's stream (one kernel per gate, or none
+ * for gates that are the identity within the zero tolerance). */
+cast_status cast_plan_apply(cast_sv *sv, const cast_plan *p);
+
+/* Number of gates after fusion, and their total operation count (either
+ * out-pointer may be NULL). */
+cast_status cast_plan_info(const cast_plan *p, int *n_gates, int64_t *total_ops);
+
+cast_status cast_plan_destroy(cast_plan *p);
+
+/* ------------------------------------------------------------------------
+ * Profiling: CUDA events around every kernel launch, on its own stream
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    char name[32];      /* kernel family, e.g. "dense_k5_c64" */
+    int64_t launches;
+    double ms;          /* sum of event-measured launch durations */
+    double bytes;       /* sum of algorithmic bytes: the amplitudes the
+                           method must read and write (2 N S per full pass) */
+    double flops;       /* sum of algorithmic floating-point operations */
+} cast_profile_entry;
+
+/* Start recording (clears earlier records).  Adds two event records per
+ * launch; meant for measurement runs. */
+cast_status cast_profile_begin(void);
+
+/* Stop recording, wait for the recorded events and return one entry per
+ * kernel family, largest total time first.  *n_out: in = capacity of out,
+ * out = number of families (CAST_ERR_ARG if the capacity is too small). */
+cast_status cast_profile_end(cast_profile_entry *out, int *n_out);
+
+/* ------------------------------------------------------------------------
  * Observables and gradients
  * ---------------------------------------------------------------------- */
 

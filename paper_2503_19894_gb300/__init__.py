@@ -17,13 +17,16 @@ from . import capi
 from .capi import (CastError, cast_adjoint_grad, cast_apply_circuit, cast_apply_gate,
                    cast_expectation, cast_fuse, cast_last_error, cast_opcount, cast_sv_copy_from_host,
                    cast_sv_copy_to_host, cast_sv_create, cast_sv_destroy, cast_sv_info,
-                   cast_sv_set_basis, cast_sv_wrap, cast_version, options)
+                   cast_sv_set_basis, cast_sv_wrap, cast_version, options, cast_plan_create,
+                   cast_plan_apply, cast_plan_info, cast_plan_destroy, cast_profile_begin,
+                   cast_profile_end)
 
 __all__ = ["capi", "CastError", "StateVector", "AdjointEnergy", "cast_adjoint_grad",
            "cast_apply_circuit", "cast_apply_gate", "cast_expectation", "cast_fuse",
            "cast_last_error", "cast_opcount", "cast_sv_copy_from_host", "cast_sv_copy_to_host",
            "cast_sv_create", "cast_sv_destroy", "cast_sv_info", "cast_sv_set_basis",
-           "cast_sv_wrap", "cast_version", "options"]
+           "cast_sv_wrap", "cast_version", "options", "cast_plan_create", "cast_plan_apply",
+           "cast_plan_info", "cast_plan_destroy", "cast_profile_begin", "cast_profile_end"]
 
 
 def _torch_dtype(dtype):

@@ -47,6 +47,11 @@ class cast_options(ctypes.Structure):
                 ("zero_tol", ctypes.c_double), ("amp_ops_per_pass", ctypes.c_int32)]
 
 
+class cast_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
 class cast_pauli_sum(ctypes.Structure):
     _fields_ = [("n_terms", ctypes.c_int32), ("coeffs", ctypes.c_void_p),
                 ("x_masks", ctypes.c_void_p), ("z_masks", ctypes.c_void_p)]
@@ -56,7 +61,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_sv_set_basis", "cast_sv_copy_to_host", "cast_sv_copy_from_host",
            "cast_apply_gate", "cast_options_default", "cast_apply_circuit", "cast_fuse",
            "cast_opcount", "cast_expectation", "cast_adjoint_grad", "cast_last_error",
-           "cast_version")
+           "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
+           "cast_plan_destroy", "cast_profile_begin", "cast_profile_end")
 
 _lib = None
 
@@ -93,6 +99,12 @@ def load(build_if_missing=True):
         "cast_adjoint_grad": (I, [P, P, P, P, P, P, P]),
         "cast_last_error": (ctypes.c_char_p, []),
         "cast_version": (ctypes.c_char_p, []),
+        "cast_plan_create": (I, [P, P, P, I, PP]),
+        "cast_plan_apply": (I, [P, P]),
+        "cast_plan_info": (I, [P, P, P]),
+        "cast_plan_destroy": (I, [P]),
+        "cast_profile_begin": (I, []),
+        "cast_profile_end": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -246,6 +258,44 @@ def cast_fuse(n, gates, params=None, opts=None):
         out.append((tuple(int(x) for x in qs[g * CAST_MAX_K:g * CAST_MAX_K + k]),
                     mats[g * slot:g * slot + d * d].reshape(d, d).copy(), int(ops[g])))
     return out
+
+
+def cast_plan_create(n, gates, params=None, opts=None, dtype="c64"):
+    p, npar = _params_arr(params)
+    circ = _Circuit(n, gates, npar)
+    o = opts if opts is not None else options()
+    h = ctypes.c_void_p()
+    _check(load().cast_plan_create(ctypes.byref(circ.c),
+                                   ctypes.c_void_p(p.ctypes.data if p is not None else None),
+                                   ctypes.byref(o), _dt(dtype), ctypes.byref(h)))
+    return h.value
+
+
+def cast_plan_apply(sv, plan):
+    _check(load().cast_plan_apply(ctypes.c_void_p(sv), ctypes.c_void_p(plan)))
+
+
+def cast_plan_info(plan):
+    n, ops = ctypes.c_int(), ctypes.c_int64()
+    _check(load().cast_plan_info(ctypes.c_void_p(plan), ctypes.byref(n), ctypes.byref(ops)))
+    return n.value, ops.value
+
+
+def cast_plan_destroy(plan):
+    _check(load().cast_plan_destroy(ctypes.c_void_p(plan)))
+
+
+def cast_profile_begin():
+    _check(load().cast_profile_begin())
+
+
+def cast_profile_end(capacity=256):
+    """Returns [{name, launches, ms, bytes, flops}], largest total time first."""
+    arr = (cast_profile_entry * capacity)()
+    n = ctypes.c_int(capacity)
+    _check(load().cast_profile_end(arr, ctypes.byref(n)))
+    return [dict(name=arr[i].name.decode(), launches=arr[i].launches, ms=arr[i].ms,
+                 bytes=arr[i].bytes, flops=arr[i].flops) for i in range(n.value)]
 
 
 def cast_opcount(matrix, zero_tol=0.0):

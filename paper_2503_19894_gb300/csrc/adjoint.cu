@@ -10,6 +10,9 @@
 // sum; they are reduced in a fixed order afterwards.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <string>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -81,6 +84,8 @@ cast_status launch_adjoint_rotation(cast_sv *psi, cast_sv *lam, int q, int pauli
     const uint64_t npairs = uint64_t(1) << (psi->n - 1);
     const int G = reduce_grid_blocks();
     const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    ProfScope ps(psi->stream, std::string("adj_rot_") + dt_name(psi->dt),
+                 4.0 * double(amp_bytes(psi->dt)) * double(npairs * 2), 28.0 * double(npairs * 2));
     if (psi->dt == CAST_C64)
         k_adj_rot<float><<<G, 256, 0, psi->stream>>>(reinterpret_cast<float2 *>(psi->data),
                                                       reinterpret_cast<float2 *>(lam->data), npairs, q,

@@ -25,6 +25,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "device.cuh"
 #include "internal.h"
@@ -203,6 +204,8 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         for (int r = 0; r < (1 << K); r++)
             for (int c = 0; c < (1 << K); c++) U.m[r][c] = to_dev<R>(g.m[size_t(r) * (1 << K) + c]);
         const int per_sm = K <= 3 ? 8 : (K == 4 ? 4 : 2);
+        ProfScope ps(sv->stream, "dense_k" + std::to_string(K) + "_" + dt_name(sv->dt),
+                     2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
         k_dense<R, K><<<(unsigned)grid_for(ns, per_sm), 256, 0, sv->stream>>>(
             reinterpret_cast<T2 *>(sv->data), ns, tg, U);
     } else {
@@ -218,6 +221,8 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         CAST_CUDA(cudaFuncSetAttribute(k_dense_tile<R, K, TS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint64_t ntiles = (ns + TS - 1) / TS;
+        ProfScope ps(sv->stream, "tile_k" + std::to_string(K) + "_" + dt_name(sv->dt),
+                     2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
         const uint64_t grid = ntiles < uint64_t(sm_count_cached()) * 4 ? ntiles : uint64_t(sm_count_cached()) * 4;
         k_dense_tile<R, K, TS><<<(unsigned)grid, 256, smem, sv->stream>>>(
             reinterpret_cast<T2 *>(sv->data), ns, tg, reinterpret_cast<const T2 *>(sv->matrices.ptr));
@@ -236,6 +241,11 @@ cast_status run_diag(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         if (K <= 5 && g.diag[j] == cplx(1.0, 0.0)) D.skip |= 1u << j;
     }
     const uint64_t N = uint64_t(1) << sv->n;
+    int touched = 0;
+    for (int j = 0; j < (1 << K); j++) touched += !((D.skip >> j) & 1) || K > 5;
+    const double frac = double(touched) / double(1 << K);
+    ProfScope ps(sv->stream, "diag_k" + std::to_string(K) + "_" + dt_name(sv->dt),
+                 2.0 * double(sizeof(T2)) * double(N) * frac, 6.0 * double(N) * frac);
     k_diag<R, K><<<(unsigned)grid_for(N, 8), 256, 0, sv->stream>>>(
         reinterpret_cast<T2 *>(sv->data), N, tg, D);
     CAST_CUDA(cudaGetLastError());
@@ -252,6 +262,12 @@ cast_status run_mono(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         M.perm[j] = (uint8_t)g.perm[j];
     }
     const uint64_t ns = uint64_t(1) << (sv->n - K);
+    int moved = 0;
+    for (int j = 0; j < (1 << K); j++) moved += g.perm[j] != j || !g.unit_phases;
+    const double frac = double(moved) / double(1 << K);
+    ProfScope ps(sv->stream, "mono_k" + std::to_string(K) + "_" + dt_name(sv->dt),
+                 2.0 * double(sizeof(T2)) * double(ns << K) * frac,
+                 g.unit_phases ? 0.0 : 6.0 * double(ns << K));
     k_mono<R, K><<<(unsigned)grid_for(ns, 8), 256, 0, sv->stream>>>(
         reinterpret_cast<T2 *>(sv->data), ns, tg, M);
     CAST_CUDA(cudaGetLastError());

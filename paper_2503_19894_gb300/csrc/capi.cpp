@@ -286,18 +286,6 @@ cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host) {
     return CAST_OK;
 }
 
-cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix) {
-    if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
-    if (!qubits || !matrix) return fail(CAST_ERR_ARG, "null qubits or matrix");
-    if (k < 1 || k > CAST_MAX_K) return fail(CAST_ERR_ARG, "gate size k must be in 1..7");
-    std::vector<cplx> m(size_t(1) << (2 * k));
-    for (size_t i = 0; i < m.size(); i++) m[i] = cplx(matrix[2 * i], matrix[2 * i + 1]);
-    PreparedGate g;
-    cast_status st = prepare_gate(sv->n, qubits, k, m.data(), 1e-12, &g);
-    if (st != CAST_OK) return st;
-    return apply_prepared(sv, g);
-}
-
 static cast_options resolve_options(const cast_options *opt, cast_dtype dt) {
     cast_options o;
     if (opt)
@@ -315,6 +303,54 @@ static cast_status check_options(const cast_options &o) {
     return CAST_OK;
 }
 
+cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix) {
+    if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
+    if (!qubits || !matrix) return fail(CAST_ERR_ARG, "null qubits or matrix");
+    if (k < 1 || k > CAST_MAX_K) return fail(CAST_ERR_ARG, "gate size k must be in 1..7");
+    std::vector<cplx> m(size_t(1) << (2 * k));
+    for (size_t i = 0; i < m.size(); i++) m[i] = cplx(matrix[2 * i], matrix[2 * i + 1]);
+    PreparedGate g;
+    cast_status st = prepare_gate(sv->n, qubits, k, m.data(), 1e-12, &g);
+    if (st != CAST_OK) return st;
+    return apply_prepared(sv, g);
+}
+
+// fuse (unless disabled) and prepare every gate of a circuit, host only
+static cast_status prepare_circuit(const cast_circuit *c, const double *params, const cast_options &o,
+                                   std::vector<PreparedGate> *prepared) {
+    cast_status st;
+    prepared->clear();
+    if (o.fusion == CAST_FUSE_NONE) {
+        prepared->resize(c->n_gates);
+        for (int g = 0; g < c->n_gates; g++) {
+            std::vector<cplx> m;
+            if ((st = gate_matrix_of(c->gates[g], params, c->n_params, &m)) != CAST_OK) return st;
+            if ((st = prepare_gate(c->n_qubits, c->gates[g].qubits, c->gates[g].k, m.data(), o.zero_tol,
+                                   &(*prepared)[g])) != CAST_OK)
+                return st;
+        }
+        return CAST_OK;
+    }
+    std::vector<FusedGate> fused;
+    if ((st = fuse_circuit(c, params, &o, &fused)) != CAST_OK) return st;
+    prepared->resize(fused.size());
+    for (size_t g = 0; g < fused.size(); g++)
+        if ((st = prepare_gate(c->n_qubits, fused[g].q, fused[g].k, fused[g].m.data(), o.zero_tol, &(*prepared)[g])) !=
+            CAST_OK)
+            return st;
+    return CAST_OK;
+}
+
+static cast_status apply_all(cast_sv *sv, const std::vector<PreparedGate> &gates) {
+    int kmax = 1;
+    for (const PreparedGate &g : gates) kmax = std::max(kmax, g.k);
+    cast_status st = ensure_gate_buffers(sv, kmax);
+    if (st != CAST_OK) return st;
+    for (const PreparedGate &g : gates)
+        if ((st = launch_gate(sv, g)) != CAST_OK) return st;
+    return CAST_OK;
+}
+
 cast_status cast_apply_circuit(cast_sv *sv, const cast_circuit *c, const double *params, const cast_options *opt) {
     if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
     cast_status st = check_circuit(c, sv->n, params);
@@ -322,24 +358,58 @@ cast_status cast_apply_circuit(cast_sv *sv, const cast_circuit *c, const double 
     const cast_options o = resolve_options(opt, sv->dt);
     if ((st = check_options(o)) != CAST_OK) return st;
     std::vector<PreparedGate> prepared;
-    if (o.fusion == CAST_FUSE_NONE) {
-        prepared.resize(c->n_gates);
-        for (int g = 0; g < c->n_gates; g++) {
-            std::vector<cplx> m;
-            if ((st = gate_matrix_of(c->gates[g], params, c->n_params, &m)) != CAST_OK) return st;
-            if ((st = prepare_gate(sv->n, c->gates[g].qubits, c->gates[g].k, m.data(), o.zero_tol, &prepared[g])) != CAST_OK)
-                return st;
-        }
-    } else {
-        std::vector<FusedGate> fused;
-        if ((st = fuse_circuit(c, params, &o, &fused)) != CAST_OK) return st;
-        prepared.resize(fused.size());
-        for (size_t g = 0; g < fused.size(); g++)
-            if ((st = prepare_gate(sv->n, fused[g].q, fused[g].k, fused[g].m.data(), o.zero_tol, &prepared[g])) != CAST_OK)
-                return st;
+    if ((st = prepare_circuit(c, params, o, &prepared)) != CAST_OK) return st;
+    return apply_all(sv, prepared);
+}
+
+}  // extern "C"
+
+struct cast_plan {
+    int n = 0;
+    std::vector<cast::PreparedGate> gates;
+    int64_t ops = 0;
+};
+
+extern "C" {
+
+cast_status cast_plan_create(const cast_circuit *c, const double *params, const cast_options *opt, cast_dtype dt,
+                             cast_plan **out) {
+    if (!out) return fail(CAST_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (!c) return fail(CAST_ERR_ARG, "null circuit");
+    if (!valid_dt(dt)) return fail(CAST_ERR_ARG, "unknown dtype");
+    if (c->n_qubits < 1 || c->n_qubits > CAST_MAX_QUBITS) return fail(CAST_ERR_ARG, "n_qubits out of range");
+    cast_status st = check_circuit(c, c->n_qubits, params);
+    if (st != CAST_OK) return st;
+    const cast_options o = resolve_options(opt, dt);
+    if ((st = check_options(o)) != CAST_OK) return st;
+    cast_plan *p = new cast_plan();
+    p->n = c->n_qubits;
+    if ((st = prepare_circuit(c, params, o, &p->gates)) != CAST_OK) {
+        delete p;
+        return st;
     }
-    for (const PreparedGate &g : prepared)
-        if ((st = apply_prepared(sv, g)) != CAST_OK) return st;
+    for (const PreparedGate &g : p->gates) p->ops += opcount(g.m.data(), g.k, o.zero_tol);
+    *out = p;
+    return CAST_OK;
+}
+
+cast_status cast_plan_apply(cast_sv *sv, const cast_plan *p) {
+    if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
+    if (!p) return fail(CAST_ERR_ARG, "null plan");
+    if (p->n != sv->n) return fail(CAST_ERR_ARG, "plan qubit count differs from the state's");
+    return apply_all(sv, p->gates);
+}
+
+cast_status cast_plan_info(const cast_plan *p, int *n_gates, int64_t *total_ops) {
+    if (!p) return fail(CAST_ERR_ARG, "null plan");
+    if (n_gates) *n_gates = (int)p->gates.size();
+    if (total_ops) *total_ops = p->ops;
+    return CAST_OK;
+}
+
+cast_status cast_plan_destroy(cast_plan *p) {
+    delete p;
     return CAST_OK;
 }
 

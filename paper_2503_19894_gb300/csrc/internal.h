@@ -53,6 +53,24 @@ namespace cast {
 
 inline size_t amp_bytes(cast_dtype dt) { return dt == CAST_C128 ? 16 : 8; }
 
+// ------------------------------------------------------------- profiling
+// Records CUDA events around one launch on stream s while profiling is on.
+class ProfScope {
+  public:
+    ProfScope(cudaStream_t s, const std::string &family, double bytes, double flops);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    bool active_ = false;
+    cudaStream_t stream_ = nullptr;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    std::string fam_;
+    double bytes_ = 0, flops_ = 0;
+};
+inline const char *dt_name(cast_dtype dt) { return dt == CAST_C64 ? "c64" : "c128"; }
+
 // ---------------------------------------------------------- prepared gates
 enum GateClass { CLS_IDENTITY = 0, CLS_DIAG = 1, CLS_MONO = 2, CLS_DENSE = 3 };
 

@@ -15,6 +15,8 @@
 // a fixed order by k_finalize, so results are bit-reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "internal.h"
 #include "device.cuh"
 
@@ -153,6 +155,8 @@ cast_status launch_pauli_group(const cast_sv *sv, uint64_t xm, int nt, const dou
     int done = 0;
     for (int start = 0; start < nt; start += kMaxTerms) {
         const int cnt = nt - start < kMaxTerms ? nt - start : kMaxTerms;
+        ProfScope ps(sv->stream, std::string("pauli_") + dt_name(sv->dt), double(amp_bytes(sv->dt)) * double(N),
+                     double(N) * (8.0 + 2.0 * cnt));
         if (sv->dt == CAST_C64) {
             PauliGroupParams<float> P;
             fill_group(&P, xm, cnt, coeffs + start, zm + start);
@@ -182,6 +186,8 @@ cast_status launch_finalize(cudaStream_t st, const double *d_partials, int per_s
 cast_status launch_inner(const cast_sv *a, const cast_sv *b, double *d_partials_re, double *d_partials_im) {
     const uint64_t N = uint64_t(1) << a->n;
     const int G = reduce_grid_blocks();
+    ProfScope ps(a->stream, std::string("inner_") + dt_name(a->dt), 2.0 * double(amp_bytes(a->dt)) * double(N),
+                 8.0 * double(N));
     if (a->dt == CAST_C64)
         k_inner<float><<<G, 256, 0, a->stream>>>(reinterpret_cast<const float2 *>(a->data),
                                                   reinterpret_cast<const float2 *>(b->data), N,
@@ -201,6 +207,8 @@ cast_status launch_pauli_apply(const cast_sv *psi, cast_sv *out, uint64_t xm, in
     bool acc = accumulate;
     for (int start = 0; start < nt; start += kMaxTerms) {
         const int cnt = nt - start < kMaxTerms ? nt - start : kMaxTerms;
+        ProfScope ps(psi->stream, std::string("pauli_apply_") + dt_name(psi->dt),
+                     double(amp_bytes(psi->dt)) * double(N) * (acc ? 3.0 : 2.0), double(N) * (6.0 + 2.0 * cnt));
         if (psi->dt == CAST_C64) {
             PauliGroupParams<float> P;
             fill_group(&P, xm, cnt, coeffs + start, zm + start);
