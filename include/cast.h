@@ -242,6 +242,34 @@ typedef struct {
 /* *out = <psi|H|psi> accumulated in FP64.  Waits for the result. */
 cast_status cast_expectation(const cast_sv *sv, const cast_pauli_sum *h, double *out);
 
+/* Scratch size of cast_expectation_noalloc, in doubles (512 KiB). */
+#define CAST_NOALLOC_SCRATCH_DOUBLES 65536
+
+/* The value of cast_expectation, computed without allocating any memory.
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot allocate: a process whose state vector already fills the GPU's
+ * memory (a 33-qubit complex128 state takes 128 GiB), code running under a
+ * memory manager that owns every device allocation, or a loop that must not
+ * stall on the device-wide synchronisation that cudaMalloc and cudaFree can
+ * cause.  cast_expectation allocates its partial-sum buffer and a pinned
+ * result buffer on first use; this call instead keeps its scratch in one
+ * fixed array of CAST_NOALLOC_SCRATCH_DOUBLES doubles that every GPU which
+ * loads the library holds until the process exits, and copies the result
+ * straight into *out.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  The state's device must be current.
+ *   - A Pauli sum needs 1 + (launches x blocks) doubles, one launch per
+ *     32 terms sharing an x_mask and 4 blocks per SM (608 on a 152-SM GB300,
+ *     so up to 107 launches); larger sums get CAST_ERR_ARG with the sizes.
+ *   - All calls share the array and it keeps the last call's contents; each
+ *     call writes every value it reads, so nothing needs clearing, but calls
+ *     whose GPU work overlaps (e.g. on two streams) race and may return wrong
+ *     values.
+ * Waits for the result. */
+cast_status cast_expectation_noalloc(const cast_sv *sv, const cast_pauli_sum *h, double *out);
+
 /* Adjoint differentiation of E(theta) = <psi0|U(theta)^dag H U(theta)|psi0>
  * for a circuit whose parametrised gates are RX/RY/RZ (exp(-i theta P / 2))
  * with param_index >= 0; fixed gates may be of any kind.

@@ -62,7 +62,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_apply_gate", "cast_options_default", "cast_apply_circuit", "cast_fuse",
            "cast_opcount", "cast_expectation", "cast_adjoint_grad", "cast_last_error",
            "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
-           "cast_plan_destroy", "cast_profile_begin", "cast_profile_end")
+           "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
+           "cast_expectation_noalloc")
 
 _lib = None
 
@@ -105,6 +106,7 @@ def load(build_if_missing=True):
         "cast_plan_destroy": (I, [P]),
         "cast_profile_begin": (I, []),
         "cast_profile_end": (I, [P, P]),
+        "cast_expectation_noalloc": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -332,6 +334,15 @@ def cast_expectation(sv, terms):
     h = _Pauli(terms)
     out = ctypes.c_double()
     _check(load().cast_expectation(ctypes.c_void_p(sv), ctypes.byref(h.s), ctypes.byref(out)))
+    return out.value
+
+
+def cast_expectation_noalloc(sv, terms):
+    """<psi|H|psi> with the scratch in the library's fixed device array (no
+    allocation; see cast.h)."""
+    h = _Pauli(terms)
+    out = ctypes.c_double()
+    _check(load().cast_expectation_noalloc(ctypes.c_void_p(sv), ctypes.byref(h.s), ctypes.byref(out)))
     return out.value
 
 

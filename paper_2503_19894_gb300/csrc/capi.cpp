@@ -64,6 +64,8 @@ cast_status apply_prepared(cast_sv *sv, const PreparedGate &g) {
     return launch_gate(sv, g);
 }
 
+}  // namespace
+
 cast_status check_sv(const cast_sv *sv) {
     if (!sv || !sv->data) return fail(CAST_ERR_ARG, "null state");
     return CAST_OK;
@@ -104,11 +106,6 @@ cast_status check_pauli(const cast_pauli_sum *h, int n) {
 }
 
 // terms grouped by x_mask, in ascending mask order (deterministic)
-struct PauliGroups {
-    std::vector<uint64_t> xm;
-    std::vector<std::vector<double>> c;
-    std::vector<std::vector<uint64_t>> z;
-};
 PauliGroups group_terms(const cast_pauli_sum *h) {
     std::map<uint64_t, size_t> at;
     PauliGroups G;
@@ -129,6 +126,8 @@ PauliGroups group_terms(const cast_pauli_sum *h) {
     }
     return G;
 }
+
+namespace {
 
 // The first kResultSlots doubles of the partials buffer hold final results.
 constexpr size_t kResultSlots = 16;

@@ -100,6 +100,17 @@ cast_status gate_matrix_of(const cast_gate &g, const double *params, int n_param
                            std::vector<cplx> *out);
 int64_t default_amp_ops_per_pass(cast_dtype dt);
 
+// ------------------------------------------------------- shared validation
+cast_status check_sv(const cast_sv *sv);
+cast_status check_pauli(const cast_pauli_sum *h, int n);
+// Pauli terms grouped by x_mask, ascending mask order
+struct PauliGroups {
+    std::vector<uint64_t> xm;
+    std::vector<std::vector<double>> c;
+    std::vector<std::vector<uint64_t>> z;
+};
+PauliGroups group_terms(const cast_pauli_sum *h);
+
 // ------------------------------------------------------------ fusion pass
 struct FusedGate {
     int k;
