@@ -155,6 +155,12 @@ def roofline(profile, mp, src, launches_per_step_kind="sustained"):
     alu_peak = fp64_tflops if top["name"].endswith("c128") else fp32_tflops
     alu_t = per_launch_flops / alu_peak / 1e12
     mem_t = per_launch_bytes / (mp["hbm_gbs"] * 1e9)
+    if top["name"].startswith("tc_"):
+        # tensor-core kernels: 3xTF32 executes 3x the algorithmic flops on the
+        # tensor pipe, whose tf32 peak is the measured bf16 peak x (1.1 / 2.25)
+        tf32 = mp.get("bf16_tflops_sustained", 1739.5) * 1.1 / 2.25
+        alu_t = 3 * per_launch_flops / (tf32 * 1e12)
+        alu_peak = tf32
     if alu_t > mem_t:
         ach = per_launch_flops / avg_s / 1e12
         r = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",

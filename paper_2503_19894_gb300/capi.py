@@ -63,7 +63,7 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_opcount", "cast_expectation", "cast_adjoint_grad", "cast_last_error",
            "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
            "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
-           "cast_expectation_noalloc")
+           "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode")
 
 _lib = None
 
@@ -107,6 +107,8 @@ def load(build_if_missing=True):
         "cast_profile_begin": (I, []),
         "cast_profile_end": (I, [P, P]),
         "cast_expectation_noalloc": (I, [P, P, P]),
+        "cast_set_tensor_mode": (I, [I]),
+        "cast_get_tensor_mode": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -358,6 +360,17 @@ def cast_adjoint_grad(psi, lam, n, gates, params, terms):
                                     ctypes.byref(h.s), ctypes.byref(energy),
                                     ctypes.c_void_p(grad.ctypes.data)))
     return energy.value, grad[:npar]
+
+
+CAST_TC_OFF, CAST_TC_TF32X3 = 0, 1
+
+
+def cast_set_tensor_mode(mode):
+    _check(load().cast_set_tensor_mode(int(mode)))
+
+
+def cast_get_tensor_mode():
+    return int(load().cast_get_tensor_mode())
 
 
 def cast_last_error():

@@ -274,7 +274,7 @@ cast_status cast_sv_copy_to_host(const cast_sv *sv, void *host) {
     if (!host) return fail(CAST_ERR_ARG, "null host buffer");
     CAST_CUDA(cudaMemcpyAsync(host, sv->data, amp_bytes(sv->dt) << sv->n, cudaMemcpyDeviceToHost, sv->stream));
     CAST_CUDA(cudaStreamSynchronize(sv->stream));
-    return CAST_OK;
+    return take_device_error();
 }
 
 cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host) {
@@ -469,7 +469,7 @@ cast_status cast_expectation(const cast_sv *csv, const cast_pauli_sum *h, double
     CAST_CUDA(cudaMemcpyAsync(sv->host_pinned, sv->partials.ptr, sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
     CAST_CUDA(cudaStreamSynchronize(sv->stream));
     *out = *reinterpret_cast<double *>(sv->host_pinned);
-    return CAST_OK;
+    return take_device_error();
 }
 
 static cast_status same_shape(const cast_sv *a, const cast_sv *b) {
@@ -597,7 +597,7 @@ cast_status cast_adjoint_grad(cast_sv *psi, cast_sv *lam, const cast_circuit *c,
     const double *hd = reinterpret_cast<const double *>(hp);
     *energy_out = hd[0];
     for (int p = 0; p < c->n_params; p++) grad_out[p] = hd[2 + p];
-    return CAST_OK;
+    return take_device_error();
 }
 
 }  // extern "C"

@@ -124,6 +124,11 @@ cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast
 // --------------------------------------------------------------- kernels
 // Queue one prepared gate on sv's stream.
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
+// Tensor-core path for dense complex64 gates (apply_tc.cu).
+bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
+cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
+// CAST_ERR_TIMEOUT (and clears the flag) if a kernel's bounded wait gave up.
+cast_status take_device_error();
 // Queue sum_t coeff_t <psi|P_t|psi> terms sharing one x_mask; partial sums
 // of FP64 go to sv->partials; returns the number of partials written.
 cast_status launch_pauli_group(const cast_sv *sv, uint64_t x_mask, int n_terms,

@@ -263,3 +263,61 @@ def test_library_owned_state_create_destroy():
     v = capi.cast_sv_copy_to_host(h)
     assert abs(v[0] - 2 ** -0.5) < 1e-7 and abs(v[8] - 2 ** -0.5) < 1e-7
     capi.cast_sv_destroy(h)
+
+
+# ------------------------------------------------- tensor-core dense gates
+
+@pytest.fixture
+def tensor_mode():
+    old = capi.cast_get_tensor_mode()
+    yield capi
+    capi.cast_set_tensor_mode(old)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_tensor_core_gate_matches_oracle(k, tensor_mode):
+    """3xTF32 tcgen05 path (complex64, k = 4, 5, n >= k + 7): every placement,
+    a single-tile state and multi-tile states with ragged CTA shares."""
+    capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
+    rng = np.random.default_rng(500 + k)
+    for n in (k + 7, k + 8, 16, 19):
+        psi0 = W.random_state(n, n + k)
+        for placement in ("low", "high", "mixed", "mixed", "mixed"):
+            qs = W.sweep_targets(n, k, placement, rng)
+            u = W.haar_unitary(k, rng)
+            got = run_gate(n, "c64", psi0, qs, u)
+            ref = oracle_gate(psi0, "c64", qs, u)
+            err = np.max(np.abs(got - ref))
+            assert err <= TOL["c64"], f"n={n} {qs}: {err:.3e}"
+
+
+def test_tensor_core_and_fp32_paths_agree(tensor_mode):
+    n = 18
+    rng = np.random.default_rng(9)
+    psi0 = W.random_state(n, 4)
+    for k in (4, 5):
+        qs = W.sweep_targets(n, k, "mixed", rng)
+        u = W.haar_unitary(k, rng)
+        capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
+        a = run_gate(n, "c64", psi0, qs, u)
+        capi.cast_set_tensor_mode(capi.CAST_TC_OFF)
+        b = run_gate(n, "c64", psi0, qs, u)
+        scale = np.max(np.abs(b))
+        assert np.max(np.abs(a - b)) <= 1e-5 * max(scale, 1e-3) * 10
+
+
+def test_tensor_core_fused_circuit(tensor_mode):
+    capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
+    n = 16
+    gates = W.random_circuit(n, 16, seed=12)
+    ref = oracle.simulate(n, gates)
+    sv = pkg.StateVector(n, "c64")
+    sv.apply_circuit(gates, fusion="size", max_k=5)
+    got = sv.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= TOL["c64"]
+    sv.close()
+
+
+def test_tensor_mode_validation(tensor_mode):
+    with pytest.raises(capi.CastError):
+        capi.cast_set_tensor_mode(7)
