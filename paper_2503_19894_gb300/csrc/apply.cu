@@ -26,6 +26,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "device.cuh"
 #include "internal.h"
@@ -211,12 +212,11 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
     } else {
         constexpr int TS = 32;
         const size_t mat_bytes = sizeof(T2) << (2 * K);
-        if (sv->matrices.bytes < mat_bytes) return fail(CAST_ERR_ARG, "matrix buffer too small");
-        // stage the converted matrix through pinned memory, then to the device
-        T2 *h = reinterpret_cast<T2 *>(sv->host_pinned);
-        CAST_CUDA(cudaStreamSynchronize(sv->stream));  // previous users of the staging buffer
-        for (size_t i = 0; i < (size_t(1) << (2 * K)); i++) h[i] = to_dev<R>(g.m[i]);
-        CAST_CUDA(cudaMemcpyAsync(sv->matrices.ptr, h, mat_bytes, cudaMemcpyHostToDevice, sv->stream));
+        std::vector<T2> h(size_t(1) << (2 * K));
+        for (size_t i = 0; i < h.size(); i++) h[i] = to_dev<R>(g.m[i]);
+        const void *dmat = nullptr;
+        cast_status st = upload_matrix(sv, h.data(), mat_bytes, &dmat);
+        if (st != CAST_OK) return st;
         const size_t smem = sizeof(T2) * (1 << K) * TS;
         CAST_CUDA(cudaFuncSetAttribute(k_dense_tile<R, K, TS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -225,7 +225,7 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
                      2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
         const uint64_t grid = ntiles < uint64_t(sm_count_cached()) * 4 ? ntiles : uint64_t(sm_count_cached()) * 4;
         k_dense_tile<R, K, TS><<<(unsigned)grid, 256, smem, sv->stream>>>(
-            reinterpret_cast<T2 *>(sv->data), ns, tg, reinterpret_cast<const T2 *>(sv->matrices.ptr));
+            reinterpret_cast<T2 *>(sv->data), ns, tg, reinterpret_cast<const T2 *>(dmat));
     }
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;

@@ -51,11 +51,22 @@ cast_status ensure_pinned(cast_sv *sv, size_t bytes) {
 }
 
 cast_status ensure_gate_buffers(cast_sv *sv, int k) {
-    if (k < 6) return CAST_OK;
-    const size_t bytes = amp_bytes(sv->dt) << (2 * CAST_MAX_K);
-    cast_status st = ensure_dev(sv, sv->matrices, bytes);
-    if (st != CAST_OK) return st;
-    return ensure_pinned(sv, bytes);
+    if (k < 6 || sv->mat_dev) return CAST_OK;
+    const size_t bytes = kMatSlotBytes * kMatSlots;
+    if (cudaMalloc(&sv->mat_dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        sv->mat_dev = nullptr;
+        return fail(CAST_ERR_OOM, "matrix ring allocation failed");
+    }
+    if (cudaMallocHost(&sv->mat_pinned, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(sv->mat_dev);
+        sv->mat_dev = nullptr;
+        sv->mat_pinned = nullptr;
+        return fail(CAST_ERR_OOM, "pinned matrix staging allocation failed");
+    }
+    for (int s = 0; s < kMatSlots; s++) CAST_CUDA(cudaEventCreateWithFlags(&sv->mat_events[s], cudaEventDisableTiming));
+    return CAST_OK;
 }
 
 cast_status apply_prepared(cast_sv *sv, const PreparedGate &g) {
@@ -65,6 +76,23 @@ cast_status apply_prepared(cast_sv *sv, const PreparedGate &g) {
 }
 
 }  // namespace
+
+cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const void **dev) {
+    if (bytes > kMatSlotBytes) return fail(CAST_ERR_ARG, "matrix larger than a ring slot");
+    cast_status st = ensure_gate_buffers(sv, CAST_MAX_K);
+    if (st != CAST_OK) return st;
+    const int s = sv->mat_next;
+    sv->mat_next = (s + 1) % kMatSlots;
+    CAST_CUDA(cudaEventSynchronize(sv->mat_events[s]));  // the slot's previous copy has completed
+    char *hp = static_cast<char *>(sv->mat_pinned) + size_t(s) * kMatSlotBytes;
+    char *dp = static_cast<char *>(sv->mat_dev) + size_t(s) * kMatSlotBytes;
+    std::memcpy(hp, host, bytes);
+    // stream order puts this copy after every kernel that read the slot before
+    CAST_CUDA(cudaMemcpyAsync(dp, hp, bytes, cudaMemcpyHostToDevice, sv->stream));
+    CAST_CUDA(cudaEventRecord(sv->mat_events[s], sv->stream));
+    *dev = dp;
+    return CAST_OK;
+}
 
 cast_status check_sv(const cast_sv *sv) {
     if (!sv || !sv->data) return fail(CAST_ERR_ARG, "null state");
@@ -252,8 +280,11 @@ cast_status cast_sv_wrap(void *device_ptr, int n_qubits, cast_dtype dt, void *cu
 cast_status cast_sv_destroy(cast_sv *sv) {
     if (!sv) return CAST_OK;
     if (sv->partials.ptr) cudaFreeAsync(sv->partials.ptr, sv->stream);
-    if (sv->matrices.ptr) cudaFreeAsync(sv->matrices.ptr, sv->stream);
     cudaError_t e = cudaStreamSynchronize(sv->stream);
+    if (sv->mat_dev) cudaFree(sv->mat_dev);
+    if (sv->mat_pinned) cudaFreeHost(sv->mat_pinned);
+    for (int s = 0; s < kMatSlots; s++)
+        if (sv->mat_events[s]) cudaEventDestroy(sv->mat_events[s]);
     if (sv->host_pinned) cudaFreeHost(sv->host_pinned);
     if (sv->owned && sv->data) cudaFree(sv->data);
     delete sv;

@@ -42,9 +42,14 @@ struct cast_sv {
     int device = 0;
     // per-state device scratch: FP64 partial sums of reductions
     cast::DeviceScratch partials;
-    // per-state device buffer for matrices of large gates (k >= 6)
-    cast::DeviceScratch matrices;
-    // pinned host staging for results and matrix uploads
+    // ring of device slots for matrices too large for launch parameters,
+    // filled from pinned staging slots; slot i is reused after its last copy
+    // completed (mat_events[i])
+    void *mat_dev = nullptr;
+    void *mat_pinned = nullptr;
+    cudaEvent_t mat_events[16] = {nullptr};
+    int mat_next = 0;
+    // pinned host buffer for results
     void *host_pinned = nullptr;
     size_t host_pinned_bytes = 0;
 };
@@ -122,6 +127,13 @@ cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast
                          std::vector<FusedGate> *out);
 
 // --------------------------------------------------------------- kernels
+// Matrix ring: kMatSlots slots of kMatSlotBytes (a 7-qubit complex128 matrix).
+constexpr int kMatSlots = 16;
+constexpr size_t kMatSlotBytes = size_t(16) << 14;
+// Copy `bytes` (<= kMatSlotBytes) of host data to a device slot, in stream
+// order on sv's stream; *dev receives the slot's device address.
+cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const void **dev);
+
 // Queue one prepared gate on sv's stream.
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).

@@ -274,9 +274,9 @@ def tensor_mode():
     capi.cast_set_tensor_mode(old)
 
 
-@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("k", [4, 5, 6])
 def test_tensor_core_gate_matches_oracle(k, tensor_mode):
-    """3xTF32 tcgen05 path (complex64, k = 4, 5, n >= k + 7): every placement,
+    """3xTF32 tcgen05 path (complex64, k = 4, 5, 6, n >= k + 7): every placement,
     a single-tile state and multi-tile states with ragged CTA shares."""
     capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
     rng = np.random.default_rng(500 + k)
@@ -295,7 +295,7 @@ def test_tensor_core_and_fp32_paths_agree(tensor_mode):
     n = 18
     rng = np.random.default_rng(9)
     psi0 = W.random_state(n, 4)
-    for k in (4, 5):
+    for k in (4, 5, 6):
         qs = W.sweep_targets(n, k, "mixed", rng)
         u = W.haar_unitary(k, rng)
         capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
@@ -321,3 +321,19 @@ def test_tensor_core_fused_circuit(tensor_mode):
 def test_tensor_mode_validation(tensor_mode):
     with pytest.raises(capi.CastError):
         capi.cast_set_tensor_mode(7)
+
+
+@pytest.mark.parametrize("dtype,k", [("c64", 7), ("c128", 6), ("c64", 6)])
+def test_many_large_gates_wrap_the_matrix_ring(dtype, k, tensor_mode):
+    """Gates whose matrices go through the device ring (16 slots): 40 in a row."""
+    n = 13
+    rng = np.random.default_rng(77 + k)
+    psi0 = W.random_state(n, 6)
+    gates = [W.Gate("U", W.sweep_targets(n, k, "mixed", rng), matrix=W.haar_unitary(k, rng)) for _ in range(40)]
+    ref = oracle.apply_circuit(psi0.astype(NP[dtype]).astype(np.complex128), gates)
+    sv = pkg.StateVector(n, dtype, init_index=None)
+    sv.from_numpy(psi0.astype(NP[dtype]))
+    sv.apply_circuit(gates, fusion="none")
+    got = sv.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= TOL[dtype] * (10 if dtype == "c64" else 1)
+    sv.close()
