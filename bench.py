@@ -126,11 +126,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = {"tc_": "apply_tc.cu", "dense_": "apply.cu", "tile_": "apply.cu", "diag_": "apply.cu",
+                  "mono_": "apply.cu", "pauli": "reduce.cu", "inner": "reduce.cu", "adj_": "adjoint.cu"}
+
+
 def read_traffic(family):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source it was taken on is unchanged (same hash), else None."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source file is unchanged since the capture (same hash), else None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2503_19894_gb300", "csrc", "apply.cu")
+    name = next((f for p, f in KERNEL_SOURCES.items() if family.startswith(p)), None)
+    if name is None:
+        return None
+    src = os.path.join(ROOT, "paper_2503_19894_gb300", "csrc", name)
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(TRAFFIC_FILE):

@@ -98,11 +98,11 @@ cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host);
  * library picks a diagonal, monomial or dense kernel for the matrix. */
 cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix);
 
-/* Arithmetic for dense complex64 gates with k = 4, 5 on states of at least
- * k + 7 qubits (process-wide setting):
- *   CAST_TC_TF32X3 (default): tcgen05 tensor cores, each fp32 operand split
- *     into a tf32 high part and an fp32 remainder, three products accumulated
- *     in fp32 (fp32-class accuracy);
+/* Arithmetic for dense, unitary complex64 gates with k = 4, 5, 6 on states of
+ * at least k + 7 qubits (process-wide setting):
+ *   CAST_TC_TF32X3 (default): tcgen05 tensor cores, each operand split into
+ *     two tf32 parts, three products accumulated in fp32, and each slice's
+ *     norm restored to its input norm (fp32-class accuracy, unbiased);
  *   CAST_TC_OFF: fp32 FMA on the CUDA cores for every gate.
  * Other gates are unaffected.  CAST_ERR_ARG for an unknown mode. */
 #define CAST_TC_OFF 0

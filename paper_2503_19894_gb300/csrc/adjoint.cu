@@ -42,25 +42,40 @@ __global__ void __launch_bounds__(256)
 k_adj_rot(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam, uint64_t npairs,
           int q, int pauli, R c, R s, double *__restrict__ partials) {
     using T2 = typename Cx<R>::T;
+    constexpr int UNR = 2;
     Acc<R> acc;
     const uint64_t bit = uint64_t(1) << q;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < npairs; t += stride) {
-        const uint64_t i0 = ((t >> q) << (q + 1)) | (t & (bit - 1));
-        const uint64_t i1 = i0 | bit;
-        const T2 p0 = psi[i0], p1 = psi[i1], l0 = lam[i0], l1 = lam[i1];
-        T2 pp0, pp1, pl0, pl1;
-        pauli_pair(pauli, p0, p1, pp0, pp1);
-        pauli_pair(pauli, l0, l1, pl0, pl1);
-        // Im(conj(l) * pp) = l.x * pp.y - l.y * pp.x
-        acc.add(l0.x * pp0.y - l0.y * pp0.x);
-        acc.add(l1.x * pp1.y - l1.y * pp1.x);
-        // U^dag v = c v + i s (P v)
-        T2 o;
-        o.x = c * p0.x - s * pp0.y; o.y = c * p0.y + s * pp0.x; psi[i0] = o;
-        o.x = c * p1.x - s * pp1.y; o.y = c * p1.y + s * pp1.x; psi[i1] = o;
-        o.x = c * l0.x - s * pl0.y; o.y = c * l0.y + s * pl0.x; lam[i0] = o;
-        o.x = c * l1.x - s * pl1.y; o.y = c * l1.y + s * pl1.x; lam[i1] = o;
+    for (uint64_t t0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t0 < npairs; t0 += stride * UNR) {
+        T2 p0[UNR], p1[UNR], l0[UNR], l1[UNR];
+        uint64_t i0[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t t = t0 + uint64_t(u) * stride;
+            i0[u] = ((t >> q) << (q + 1)) | (t & (bit - 1));
+            if (t < npairs) {
+                p0[u] = psi[i0[u]];
+                p1[u] = psi[i0[u] | bit];
+                l0[u] = lam[i0[u]];
+                l1[u] = lam[i0[u] | bit];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (t0 + uint64_t(u) * stride >= npairs) continue;
+            T2 pp0, pp1, pl0, pl1;
+            pauli_pair(pauli, p0[u], p1[u], pp0, pp1);
+            pauli_pair(pauli, l0[u], l1[u], pl0, pl1);
+            // Im(conj(l) * pp) = l.x * pp.y - l.y * pp.x
+            acc.add(l0[u].x * pp0.y - l0[u].y * pp0.x);
+            acc.add(l1[u].x * pp1.y - l1[u].y * pp1.x);
+            // U^dag v = c v + i s (P v)
+            T2 o;
+            o.x = c * p0[u].x - s * pp0.y; o.y = c * p0[u].y + s * pp0.x; psi[i0[u]] = o;
+            o.x = c * p1[u].x - s * pp1.y; o.y = c * p1[u].y + s * pp1.x; psi[i0[u] | bit] = o;
+            o.x = c * l0[u].x - s * pl0.y; o.y = c * l0[u].y + s * pl0.x; lam[i0[u]] = o;
+            o.x = c * l1[u].x - s * pl1.y; o.y = c * l1[u].y + s * pl1.x; lam[i0[u] | bit] = o;
+        }
     }
     const double v = block_sum(acc.value());
     if (threadIdx.x == 0) partials[blockIdx.x] = v;

@@ -133,18 +133,64 @@ struct DiagVec {
     uint32_t skip;  // bit j set: d[j] == 1, amplitudes with local index j untouched
 };
 
+// 16-byte vectors: 2 complex64 or 1 complex128 amplitudes per access.
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int A = 2; };
+template <> struct Vec16<double> { using T = double2; static constexpr int A = 1; };
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T vec_amp(const typename Vec16<R>::T &v, int a);
+template <> __device__ __forceinline__ float2 vec_amp<float>(const float4 &v, int a) {
+    return a == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+}
+template <> __device__ __forceinline__ double2 vec_amp<double>(const double2 &v, int) { return v; }
+template <typename R>
+__device__ __forceinline__ void vec_set(typename Vec16<R>::T &v, int a, typename Cx<R>::T x);
+template <> __device__ __forceinline__ void vec_set<float>(float4 &v, int a, float2 x) {
+    if (a == 0) { v.x = x.x; v.y = x.y; } else { v.z = x.x; v.w = x.y; }
+}
+template <> __device__ __forceinline__ void vec_set<double>(double2 &v, int, double2 x) { v = x; }
+
+// Each thread takes UNR 16-byte vectors per round (grid stride apart), issues
+// all their loads before any arithmetic, and skips a vector whose amplitudes
+// all have diagonal entry 1 (neither read nor written).
 template <typename R, int K>
 __global__ void __launch_bounds__(256)
 k_diag(typename Cx<R>::T *__restrict__ sv, uint64_t N, Targets tg,
        const __grid_constant__ DiagVec<R, K> D) {
-    using T2 = typename Cx<R>::T;
+    using V = typename Vec16<R>::T;
+    constexpr int A = Vec16<R>::A, UNR = 4;
+    V *vp = reinterpret_cast<V *>(sv);
+    const uint64_t nvec = N / A;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
-        int j = 0;
+    for (uint64_t v0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; v0 < nvec; v0 += stride * UNR) {
+        V v[UNR];
+        int j[UNR][A];
+        bool act[UNR];
 #pragma unroll
-        for (int b = 0; b < K; b++) j |= int((i >> tg.q[b]) & 1) << b;
-        if ((K <= 5) && ((D.skip >> j) & 1)) continue;
-        sv[i] = cmul(D.d[j], sv[i]);
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t iv = v0 + uint64_t(u) * stride;
+            act[u] = false;
+            if (iv < nvec) {
+#pragma unroll
+                for (int a = 0; a < A; a++) {
+                    const uint64_t x = iv * A + a;
+                    int jj = 0;
+#pragma unroll
+                    for (int b = 0; b < K; b++) jj |= int((x >> tg.q[b]) & 1) << b;
+                    j[u][a] = jj;
+                    act[u] |= (K > 5) || !((D.skip >> jj) & 1);
+                }
+                if (act[u]) v[u] = vp[iv];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (!act[u]) continue;
+#pragma unroll
+            for (int a = 0; a < A; a++) vec_set<R>(v[u], a, cmul(D.d[j[u][a]], vec_amp<R>(v[u], a)));
+            vp[v0 + uint64_t(u) * stride] = v[u];
+        }
     }
 }
 

@@ -8,10 +8,19 @@
 //     Y^T (128 x 2^(k+1)) = X^T (128 x 2^(k+1)) * W^T,
 // one tcgen05.mma chain with M = 128 (TMEM lane = slice), N = K = 2^(k+1).
 //
-// Precision: 3xTF32.  Each fp32 operand x is split into hi = tf32(x) and
-// lo = x - hi (exact); the three products lo*W_hi + hi*W_lo + hi*W_hi are
-// accumulated in fp32 in TMEM, giving fp32-class accuracy (the dropped lo*lo
-// term and the truncation of lo are ~2^-22 relative).
+// Precision: 3xTF32.  Each operand x is split into hi = tf32(x) and
+// lo = tf32(x - hi), both rounded to nearest; the three products lo*W_hi +
+// hi*W_lo + hi*W_hi are accumulated in fp32 in TMEM, giving fp32-class
+// accuracy (the dropped lo*lo term and the rounding of lo are ~2^-22
+// relative).  Rounding lo (rather than letting the tensor cores truncate it)
+// removes one bias.  The tensor cores' fp32 accumulation itself truncates
+// toward zero, which shrinks every output slightly (measured: ~2^-23 of the
+// norm per gate, growing with k).  A unitary gate preserves the norm of every
+// slice exactly, so each slice's outputs are rescaled by |x| / |y| (both norms
+// summed with a compensated fp32 pair); what remains is unbiased rounding
+// noise.  The correction is applied as y + y * delta with delta formed as a
+// small number, so it is not quantised to the fp32 spacing near 1.  Only gates
+// that are unitary to 1e-9 take this path.
 //
 // Data path per tile: thread (warp w, lane i) owns slice 32*(w%4) + i, i.e.
 // TMEM lane 32*(w%4) + i, and 16 of its members (warp group w/4).  It gathers
@@ -93,9 +102,12 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     uint8_t *sWlo = sWhi + NK * NK * 4;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sWlo + NK * NK * 4);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    float2 *xnorm = reinterpret_cast<float2 *>(tslot + 2);   // [GROUPS][128] compensated |x|^2 parts
+    float2 *ynorm = xnorm + S::GROUPS * 128;                 // [GROUPS][128] compensated |y|^2 parts
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, j0 = (warp >> 2) * MPT;
+    const int quarter = warp & 3, group = warp >> 2, j0 = group * MPT;
+    const int row = 32 * quarter + lane;
 
     // ---- prologue: W_hi / W_lo (SW128 K-major), barrier, TMEM
     for (int idx = tid; idx < NK * NK; idx += S::NT) {
@@ -152,12 +164,20 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
             v[2 * m + 1] = tc::to_tf32(cur[m].y);
         }
         tc::tmem_st<2 * MPT>(lane_addr + COL_AH + 2 * j0, v);
+        // the remainder is rounded to tf32 as well: the tensor cores would
+        // otherwise truncate it, a bias that shrinks the norm gate after gate
 #pragma unroll
         for (int m = 0; m < MPT; m++) {
-            v[2 * m] = cur[m].x - v[2 * m];
-            v[2 * m + 1] = cur[m].y - v[2 * m + 1];
+            v[2 * m] = tc::to_tf32(cur[m].x - v[2 * m]);
+            v[2 * m + 1] = tc::to_tf32(cur[m].y - v[2 * m + 1]);
         }
         tc::tmem_st<2 * MPT>(lane_addr + COL_AL + 2 * j0, v);
+        {
+            Acc<float> xs;
+#pragma unroll
+            for (int m = 0; m < MPT; m++) xs.add(cur[m].x * cur[m].x + cur[m].y * cur[m].y);
+            xnorm[group * 128 + row] = make_float2(xs.hi, xs.lo);
+        }
         tc::tmem_wait_st();
         // ---- prefetch the next tile; the loads stay in flight meanwhile
         const uint64_t next = tile + gridDim.x;
@@ -188,12 +208,35 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         }
         phase ^= 1u;
         tc::fence_after_sync();
-        // ---- accumulator -> registers -> HBM
+        // ---- accumulator -> registers; restore the slice norm; -> HBM
         tc::tmem_ld<2 * MPT>(lane_addr + 2 * j0, v);
         {
-            const uint64_t b = slice_base<K>(tile * 128 + uint64_t(32 * quarter + lane), tg);
+            Acc<float> ys;
 #pragma unroll
-            for (int m = 0; m < MPT; m++) __stcs(&sv[b + member_off(m)], make_float2(v[2 * m], v[2 * m + 1]));
+            for (int m = 0; m < MPT; m++) ys.add(v[2 * m] * v[2 * m] + v[2 * m + 1] * v[2 * m + 1]);
+            ynorm[group * 128 + row] = make_float2(ys.hi, ys.lo);
+        }
+        __syncthreads();
+        {
+            Acc<float> X, Y;
+#pragma unroll
+            for (int gq = 0; gq < S::GROUPS; gq++) {
+                const float2 a = xnorm[gq * 128 + row], b = ynorm[gq * 128 + row];
+                X.add(a.x); X.add(a.y);
+                Y.add(b.x); Y.add(b.y);
+            }
+            // y <- y * sqrt(X / Y) = y + y * delta with delta = (X - Y) / (2 Y) to
+            // first order (|delta| ~ 1e-7; the second-order term is ~1e-14).
+            // delta is formed as a small number (X.hi - Y.hi is exact when the
+            // two are close) so the correction keeps full fp32 precision; a
+            // scale factor near 1 would be quantised to multiples of 2^-23.
+            float delta = 0.0f;
+            if (Y.hi > 0.0f && X.hi > 0.0f) delta = 0.5f * ((X.hi - Y.hi) + (X.lo - Y.lo)) / Y.hi;
+            const uint64_t b = slice_base<K>(tile * 128 + uint64_t(row), tg);
+#pragma unroll
+            for (int m = 0; m < MPT; m++)
+                __stcs(&sv[b + member_off(m)],
+                       make_float2(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1])));
         }
         tile = next;
 #pragma unroll
@@ -224,7 +267,7 @@ float host_tf32(float x) {
 template <int K>
 size_t tc_smem_bytes() {
     using S = TcShape<K>;
-    const size_t need = 1024 + size_t(S::NK) * S::NK * 4 * 2 + 64;
+    const size_t need = 1024 + size_t(S::NK) * S::NK * 4 * 2 + 64 + 2 * 8 * 128 * S::GROUPS;
     // at most CTAS_PER_SM resident CTAs per SM (228 KB of shared memory each)
     const size_t floor = (228 * 1024) / (S::CTAS_PER_SM + 1) + 1024;
     return need > floor ? need : floor;
@@ -241,7 +284,7 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
             const float hr = host_tf32((float)u.real()), hi = host_tf32((float)u.imag());
             hl[size_t(r) * D + c] = make_float2(hr, hi);
             hl[(size_t(1) << (2 * K)) + size_t(r) * D + c] =
-                make_float2((float)(u.real() - (double)hr), (float)(u.imag() - (double)hi));
+                make_float2(host_tf32((float)(u.real() - (double)hr)), host_tf32((float)(u.imag() - (double)hi)));
         }
     TcMat<K> U;
     if constexpr (K <= 5) {
@@ -270,7 +313,7 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
 }  // namespace
 
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g) {
-    return g_tensor_mode.load() == CAST_TC_TF32X3 && sv->dt == CAST_C64 && g.cls == CLS_DENSE &&
+    return g_tensor_mode.load() == CAST_TC_TF32X3 && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary &&
            g.k >= 4 && g.k <= 6 && sv->n >= g.k + 7;
 }
 

@@ -162,6 +162,18 @@ cast_status prepare_gate(int n, const int *qubits, int k, const cplx *matrix, do
             g->m[size_t(r) * d + c] = cplx(re, im);
         }
 
+    // unitarity (the tensor-core path relies on it, see apply_tc.cu)
+    {
+        double worst = 0.0;
+        for (int r = 0; r < d && worst <= 1e-9; r++)
+            for (int c = 0; c < d; c++) {
+                cplx s(0.0, 0.0);
+                for (int t = 0; t < d; t++) s += std::conj(g->m[size_t(t) * d + r]) * g->m[size_t(t) * d + c];
+                worst = std::max(worst, std::abs(s - (r == c ? cplx(1.0, 0.0) : cplx(0.0, 0.0))));
+            }
+        g->unitary = worst <= 1e-9;
+    }
+
     // classify: diagonal, monomial (one non-zero per row and column), dense
     bool diag = true;
     for (int r = 0; r < d && diag; r++)

@@ -90,6 +90,7 @@ struct PreparedGate {
     std::vector<int> perm;      // CLS_MONO: row r reads column perm[r]
     std::vector<cplx> phase;    // CLS_MONO: value of the non-zero in row r
     bool unit_phases = false;   // CLS_MONO: every phase is exactly 1
+    bool unitary = false;       // max |U^dag U - I| <= 1e-9
 };
 
 // Validate + sort + classify.  Returns CAST_OK or CAST_ERR_ARG.

@@ -47,29 +47,49 @@ struct PauliGroupParams {
     R ci[kMaxTerms];  // coefficient times -Im(i^ny)
 };
 
-// sum_x [A(x) Re w(x) + B(x) Im w(x)],  w = conj(psi[x ^ xm]) psi[x]
+// sum_x [A(x) Re w(x) + B(x) Im w(x)],  w = conj(psi[x ^ xm]) psi[x].
+// UNR independent loads per thread per round keep enough bytes in flight.
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_pauli(const typename Cx<R>::T *__restrict__ sv, uint64_t N,
         const __grid_constant__ PauliGroupParams<R> P, double *__restrict__ partials) {
     using T2 = typename Cx<R>::T;
-    Acc<R> acc;
+    constexpr int UNR = 8;
+    // two independent accumulators (alternating rounds) shorten the
+    // dependency chain; each round's UNR products are summed in the state's
+    // precision first, then added to the compensated accumulator once
+    Acc<R> acc0, acc1;
+    int round = 0;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
-        const T2 a = sv[x];
-        const T2 b = P.xm ? sv[x ^ P.xm] : a;
-        const R wr = b.x * a.x + b.y * a.y;
-        const R wi = b.x * a.y - b.y * a.x;
-        R A = 0, B = 0;
-        for (int t = 0; t < P.nt; t++) {
-            const bool odd = __popcll(x & P.z[t]) & 1;
-            A += odd ? -P.cr[t] : P.cr[t];
-            B += odd ? -P.ci[t] : P.ci[t];
+    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < N; x0 += stride * UNR, round++) {
+        T2 a[UNR], b[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t x = x0 + uint64_t(u) * stride;
+            if (x < N) {
+                a[u] = sv[x];
+                b[u] = P.xm ? sv[x ^ P.xm] : a[u];
+            }
         }
-        acc.add(A * wr);
-        acc.add(B * wi);
+        R part = 0;
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t x = x0 + uint64_t(u) * stride;
+            if (x >= N) continue;
+            const R wr = b[u].x * a[u].x + b[u].y * a[u].y;
+            const R wi = b[u].x * a[u].y - b[u].y * a[u].x;
+            R A = 0, B = 0;
+            for (int t = 0; t < P.nt; t++) {
+                const bool odd = __popcll(x & P.z[t]) & 1;
+                A += odd ? -P.cr[t] : P.cr[t];
+                B += odd ? -P.ci[t] : P.ci[t];
+            }
+            part += A * wr + B * wi;
+        }
+        if (round & 1) acc1.add(part);
+        else acc0.add(part);
     }
-    double v = block_sum(acc.value());
+    double v = block_sum(acc0.value() + acc1.value());
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
@@ -79,14 +99,24 @@ __global__ void __launch_bounds__(256)
 k_inner(const typename Cx<R>::T *__restrict__ a, const typename Cx<R>::T *__restrict__ b, uint64_t N,
         double *__restrict__ partials_re, double *__restrict__ partials_im) {
     using T2 = typename Cx<R>::T;
+    constexpr int UNR = 4;
     Acc<R> re, im;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
-        const T2 u = a[x], v = b[x];
-        re.add(u.x * v.x);
-        re.add(u.y * v.y);
-        im.add(u.x * v.y);
-        im.add(-u.y * v.x);
+    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < N; x0 += stride * UNR) {
+        T2 u[UNR], v[UNR];
+#pragma unroll
+        for (int k = 0; k < UNR; k++) {
+            const uint64_t x = x0 + uint64_t(k) * stride;
+            if (x < N) { u[k] = a[x]; v[k] = b[x]; }
+        }
+#pragma unroll
+        for (int k = 0; k < UNR; k++) {
+            if (x0 + uint64_t(k) * stride >= N) continue;
+            re.add(u[k].x * v[k].x);
+            re.add(u[k].y * v[k].y);
+            im.add(u[k].x * v[k].y);
+            im.add(-u[k].y * v[k].x);
+        }
     }
     double r = block_sum(re.value());
     double i = block_sum(im.value());
@@ -102,26 +132,39 @@ __global__ void __launch_bounds__(256)
 k_pauli_apply(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ out,
               uint64_t N, const __grid_constant__ PauliGroupParams<R> P, int accumulate) {
     using T2 = typename Cx<R>::T;
+    constexpr int UNR = 4;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
-        const uint64_t src = x ^ P.xm;
-        const T2 v = psi[src];
-        // factor f = sum_t (-1)^{popc(src & z_t)} c_t i^{ny_t} = fr + i fi
-        R fr = 0, fi = 0;
-        for (int t = 0; t < P.nt; t++) {
-            const bool odd = __popcll(src & P.z[t]) & 1;
-            fr += odd ? -P.cr[t] : P.cr[t];
-            fi += odd ? P.ci[t] : -P.ci[t];
+    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < N; x0 += stride * UNR) {
+        T2 v[UNR], o[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t x = x0 + uint64_t(u) * stride;
+            if (x < N) {
+                v[u] = psi[x ^ P.xm];
+                if (accumulate) o[u] = out[x];
+            }
         }
-        T2 y;
-        y.x = fr * v.x - fi * v.y;
-        y.y = fr * v.y + fi * v.x;
-        if (accumulate) {
-            const T2 o = out[x];
-            y.x += o.x;
-            y.y += o.y;
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t x = x0 + uint64_t(u) * stride;
+            if (x >= N) continue;
+            const uint64_t src = x ^ P.xm;
+            // factor f = sum_t (-1)^{popc(src & z_t)} c_t i^{ny_t} = fr + i fi
+            R fr = 0, fi = 0;
+            for (int t = 0; t < P.nt; t++) {
+                const bool odd = __popcll(src & P.z[t]) & 1;
+                fr += odd ? -P.cr[t] : P.cr[t];
+                fi += odd ? P.ci[t] : -P.ci[t];
+            }
+            T2 y;
+            y.x = fr * v[u].x - fi * v[u].y;
+            y.y = fr * v[u].y + fi * v[u].x;
+            if (accumulate) {
+                y.x += o[u].x;
+                y.y += o[u].y;
+            }
+            out[x] = y;
         }
-        out[x] = y;
     }
 }
 
