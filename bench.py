@@ -16,6 +16,10 @@ the adaptive agglomerative fusion into gates of at most 5 qubits, then <Z_0>.
   cpu_baseline  the oracle (plain FP64 C, OpenMP) on the host cores, applying
           the unfused QFT gates to the same 30-qubit state for a bounded time
 
+  vqa     the second half of the metric: batched variational energies and
+          gradients per second (256 ansatz instances of 16..24 qubits) and
+          26-qubit adjoint gradients, against the plain per-instance loop
+
 --impl reference times the oracle alone, as it stands, on the same workload.
 Multi-GPU (torchrun): replicas, one state per GPU, no collective on the data
 path; value sums all ranks' bytes over the slowest rank's time.
@@ -53,6 +57,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-vqa", action="store_true")
     return p.parse_args()
 
 
@@ -180,6 +185,92 @@ def roofline(profile, mp, src, launches_per_step_kind="sustained"):
               "bytes_per_launch": per_launch_bytes, "hbm_gbs_achieved": round(gbs, 1),
               "traffic": read_traffic(top["name"])})
     return r
+
+
+def _time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
+
+
+def vqa_bench():
+    """Batched VQA (256 hardware-efficient-ansatz instances, n ~ U{16..24},
+    10 layers, H = sum ZZ + 0.5 sum X) and 26-qubit adjoint gradients (20
+    layers, 1040 parameters, H = sum ZZ + 0.7 sum X): batched / adjoint
+    throughput against the plain per-instance loop through the single-state
+    API (cast_apply_circuit gate by gate + cast_expectation)."""
+    import math
+
+    import paper_2503_19894_gb300 as pkg
+    from paper_2503_19894_gb300 import capi
+    out = {}
+    batch = W.vqa_batch(256, 16, 24, 10, seed=3)
+    ns = [n for n, _, _ in batch]
+    theta = np.concatenate([p for _, _, p in batch])
+    for dt in ("c64", "c128"):
+        b = capi.cast_hea_create(ns, 10, dt, with_grad=True)
+        t_e = _time(lambda: capi.cast_hea_energy(b, theta, 1.0, 0.5, len(ns)), 3)
+        t_g = _time(lambda: capi.cast_hea_grad(b, theta, 1.0, 0.5, len(ns)), 3)
+        capi.cast_hea_destroy(b)
+
+        per_inst = []
+
+        def plain():
+            per_inst.clear()
+            for n, gates, p in batch:
+                t0 = time.perf_counter()
+                sv = pkg.StateVector(n, dt)
+                sv.apply_circuit(gates, p, fusion="none")
+                sv.expectation(W.tfim_hamiltonian(n, 0.5))  # waits for the result
+                sv.close()
+                per_inst.append(time.perf_counter() - t0)
+        t_p = _time(plain, 1)
+        # parameter shift: 2 energy evaluations per parameter, per instance
+        t_ps = sum(2 * 2 * n * 10 * ti for n, ti in zip(ns, per_inst))
+        out[f"batched_{dt}"] = {
+            "instances": len(ns), "n_range": [16, 24], "layers": 10,
+            "energies_per_s": round(len(ns) / t_e, 1), "grads_per_s": round(len(ns) / t_g, 1),
+            "plain_energies_per_s": round(len(ns) / t_p, 1),
+            "plain_grads_per_s_param_shift": round(len(ns) / t_ps, 5),
+            "grad_speedup_vs_param_shift": round(t_ps / t_g, 1),
+            "energy_speedup_vs_plain": round(t_p / t_e, 1),
+            "ms": {"batched_energy": round(t_e * 1e3, 2), "batched_grad": round(t_g * 1e3, 2),
+                   "plain_energy_loop": round(t_p * 1e3, 1)}}
+    n, layers = 26, 20
+    gates, npar = W.hea_ansatz(n, layers)
+    th = W.uniform_params(npar, -math.pi, math.pi, 7)
+    H = W.tfim_hamiltonian(n, 0.7)
+    for dt in ("c64", "c128"):
+        b = capi.cast_hea_create([n], layers, dt, with_grad=True)
+        t_f = _time(lambda: capi.cast_hea_energy(b, th, 1.0, 0.7, 1), 3)
+        t_a = _time(lambda: capi.cast_hea_grad(b, th, 1.0, 0.7, 1), 3)
+        capi.cast_hea_destroy(b)
+        psi, lam = pkg.StateVector(n, dt), pkg.StateVector(n, dt, init_index=None)
+        t_pa = _time(lambda: pkg.cast_adjoint_grad(psi.handle, lam.handle, n, gates, th, H), 1)
+
+        def fwd_plain():
+            psi.set_basis(0)
+            psi.apply_circuit(gates, th, fusion="none")
+            psi.expectation(H)
+        t_pf = _time(fwd_plain, 1)
+        psi.close()
+        lam.close()
+        out[f"adjoint26_{dt}"] = {
+            "n_qubits": n, "layers": layers, "params": npar,
+            "grads_per_s": round(1.0 / t_a, 2), "forward_per_s": round(1.0 / t_f, 2),
+            "adjoint_over_forward": round(t_a / t_f, 2),
+            "per_gate_adjoint_grads_per_s": round(1.0 / t_pa, 3),
+            "per_gate_adjoint_over_per_gate_forward": round(t_pa / t_pf, 2),
+            "plain_param_shift_grads_per_s": round(1.0 / (2 * npar * t_pf), 5),
+            "speedup_vs_param_shift": round(2 * npar * t_pf / t_a, 1),
+            "ms": {"tile_forward": round(t_f * 1e3, 2), "tile_adjoint": round(t_a * 1e3, 2),
+                   "per_gate_forward": round(t_pf * 1e3, 2), "per_gate_adjoint": round(t_pa * 1e3, 2)}}
+    return out
 
 
 def cpu_baseline(n, qft, seconds):
@@ -330,6 +421,8 @@ def main():
                 "clocks": clk.summary(),
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in p.items()}
                             for p in prof[:8]]}
+        if world == 1 and not a.no_vqa:
+            line["vqa"] = vqa_bench()
         if world == 1 and not a.no_cpu:
             line["cpu_baseline"] = cpu_baseline(n, qft, a.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -299,6 +299,48 @@ cast_status cast_expectation_noalloc(const cast_sv *sv, const cast_pauli_sum *h,
 cast_status cast_adjoint_grad(cast_sv *psi, cast_sv *lam, const cast_circuit *c, const double *params,
                               const cast_pauli_sum *h, double *energy_out, double *grad_out);
 
+/* ------------------------------------------------------------------------
+ * Batched variational circuits: the hardware-efficient ansatz
+ * ---------------------------------------------------------------------- */
+
+/* A batch of instances of the hardware-efficient ansatz, each with its own
+ * qubit count n_i (2..30) and parameters: per layer RY(theta) on every qubit,
+ * RZ(phi) on every qubit, then CZ(i, i+1) for i < n_i - 1, starting from
+ * |0...0>.  Instance i's 2 n_i L parameters are, per layer l, the n_i RY
+ * angles then the n_i RZ angles (index 2 n_i l + q and 2 n_i l + n_i + q);
+ * the batch's parameter array concatenates the instances in order.
+ * Energies are of H = zz sum_{i<n-1} Z_i Z_{i+1} + hx sum_i X_i (open
+ * boundary), accumulated in FP64.  These are the training forms of the same
+ * gate arithmetic (Eq. 3); the paper's VQA motivation is in Section I.
+ *
+ * The gates of a group of up to T - 5 qubits are applied while a tile of 2^T
+ * amplitudes is resident in shared memory (T = 12 complex64, 11
+ * complex128), so a layer costs ~n/(T-5) passes over the states instead of
+ * 3n - 1; all instances share each launch, and the launch sequence is
+ * captured once in a CUDA graph and replayed for every parameter set.
+ * with_grad allocates the second state arena that adjoint gradients need. */
+typedef struct cast_hea cast_hea;
+
+cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers, cast_dtype dt,
+                            int with_grad, void *cuda_stream, cast_hea **out);
+
+/* energies[i] = <psi_i|H|psi_i>.  params: all instances' parameters.
+ * Waits for the result. */
+cast_status cast_hea_energy(cast_hea *b, const double *params, double zz, double hx, double *energies);
+
+/* Energies plus adjoint gradients (same layout as params): forward sweep,
+ * lambda = H psi, then a backward sweep that un-applies the gates from psi
+ * and lambda and forms Im<lambda|P|psi> for every rotation (two state
+ * vectors per instance).  CAST_ERR_ARG if the batch was created without
+ * with_grad.  Waits for the result. */
+cast_status cast_hea_grad(cast_hea *b, const double *params, double zz, double hx, double *energies,
+                          double *grads);
+
+/* Total parameter count and the largest number of passes per layer. */
+cast_status cast_hea_info(const cast_hea *b, int *n_params, int *n_passes_per_layer_max);
+
+cast_status cast_hea_destroy(cast_hea *b);
+
 /* Thread-local description of the last failure on this host thread. */
 const char *cast_last_error(void);
 

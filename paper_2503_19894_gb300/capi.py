@@ -63,7 +63,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_opcount", "cast_expectation", "cast_adjoint_grad", "cast_last_error",
            "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
            "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
-           "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode")
+           "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode",
+           "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy")
 
 _lib = None
 
@@ -109,6 +110,11 @@ def load(build_if_missing=True):
         "cast_expectation_noalloc": (I, [P, P, P]),
         "cast_set_tensor_mode": (I, [I]),
         "cast_get_tensor_mode": (I, []),
+        "cast_hea_create": (I, [I, P, I, I, I, P, PP]),
+        "cast_hea_energy": (I, [P, P, D, D, P]),
+        "cast_hea_grad": (I, [P, P, D, D, P, P]),
+        "cast_hea_info": (I, [P, P, P]),
+        "cast_hea_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -371,6 +377,43 @@ def cast_set_tensor_mode(mode):
 
 def cast_get_tensor_mode():
     return int(load().cast_get_tensor_mode())
+
+
+# --------------------------------------------- batched hardware-efficient ansatz
+
+def cast_hea_create(n_qubits, layers, dtype="c64", with_grad=False, stream=0):
+    n = np.ascontiguousarray(n_qubits, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().cast_hea_create(int(n.size), ctypes.c_void_p(n.ctypes.data), int(layers), _dt(dtype),
+                                  int(bool(with_grad)), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def cast_hea_info(b):
+    npar, npass = ctypes.c_int(), ctypes.c_int()
+    _check(load().cast_hea_info(ctypes.c_void_p(b), ctypes.byref(npar), ctypes.byref(npass)))
+    return npar.value, npass.value
+
+
+def cast_hea_energy(b, params, zz, hx, n_instances):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    e = np.zeros(n_instances, dtype=np.float64)
+    _check(load().cast_hea_energy(ctypes.c_void_p(b), ctypes.c_void_p(p.ctypes.data), float(zz), float(hx),
+                                  ctypes.c_void_p(e.ctypes.data)))
+    return e
+
+
+def cast_hea_grad(b, params, zz, hx, n_instances):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    e = np.zeros(n_instances, dtype=np.float64)
+    g = np.zeros(p.size, dtype=np.float64)
+    _check(load().cast_hea_grad(ctypes.c_void_p(b), ctypes.c_void_p(p.ctypes.data), float(zz), float(hx),
+                                ctypes.c_void_p(e.ctypes.data), ctypes.c_void_p(g.ctypes.data)))
+    return e, g
+
+
+def cast_hea_destroy(b):
+    _check(load().cast_hea_destroy(ctypes.c_void_p(b)))
 
 
 def cast_last_error():

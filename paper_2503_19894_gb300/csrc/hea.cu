@@ -1,0 +1,847 @@
+// Batched variational circuits: the hardware-efficient ansatz (per layer: RY
+// on every qubit, RZ on every qubit, then CZ(i, i+1) for i < n-1) on many
+// instances of uneven qubit counts, with energies of
+//     H = zz * sum_i Z_i Z_{i+1} + hx * sum_i X_i   (open boundary)
+// and adjoint gradients.
+//
+// Tile executor.  Per-gate passes would read and write the whole state 3n-1
+// times per layer.  Here a tile of 2^T amplitudes (T = 12 for complex64,
+// 11 for complex128: 32 KB) is loaded into shared memory once per "group" of
+// qubits and every rotation of that group is applied while the tile is
+// resident:
+//   group 0      qubits 0 .. T-1            (the tile is contiguous)
+//   group g >= 1 qubits T+(g-1)G .. T+gG-1  (G = T-5), tile = those qubits
+//                plus index bits 0..4 (runs of 32 amplitudes stay coalesced)
+// A layer is then ~n/G passes.  Rotations on different qubits commute, so the
+// order "RY on all, RZ on all" equals "RZ_q RY_q" qubit by qubit; the CZ ladder
+// is diagonal and is applied, as a sign from the global index, when the last
+// group's tile is stored.  Inside a tile the rotations run in rounds of up to
+// three qubits: each thread gathers the 8 amplitudes of a sub-slice from
+// shared memory, applies the three 2x2 gates in registers and scatters them
+// back, so shared memory is crossed once per three qubits.
+//
+// Energies: one read-only pass per group; group 0 also forms the diagonal
+// ZZ part; the X_q terms of a group's qubits are formed from amplitude pairs
+// inside the tile.  lambda = H psi is built the same way (group 0 writes, the
+// others accumulate).  The adjoint backward sweep visits the layers in reverse
+// and, per layer, the groups in reverse (the last group first, undoing the CZ
+// ladder at load); for each qubit it forms Im<lam|Z|psi> then un-applies RZ,
+// then Im<lam|Y|psi> and un-applies RY, on psi and lam together.  Because the
+// gradient of a gate is unchanged by reordering gates that commute with it,
+// processing qubit by qubit gives the gradients of the layer-ordered circuit.
+//
+// Work distribution: one launch per (layer, group) covers the tiles of every
+// instance that has that group; each CTA takes a contiguous range of the tile
+// list, so it mostly stays within one instance.  Per-instance energy and
+// gradient sums go through shared-memory accumulators flushed with FP64
+// atomics when the instance changes.  The whole sequence of launches is
+// captured once into a CUDA graph and replayed for every parameter set.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace cast {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxGroups = 8;
+
+struct HeaInst {
+    uint64_t off;      // amplitude offset of the state in the arena
+    int n;
+    int ngroups;
+    int param_off;     // offset of this instance's 2 n L parameters
+    int rot_off;       // offset of its L x n rotation entries
+};
+
+template <typename R>
+struct Rot {  // RY: [[c, -s], [s, c]];  RZ: diag(cz - i sz, cz + i sz)
+    R cy, sy, cz, sz;
+};
+
+// one launch = (layer, group); instances with that group and their tile ranges
+struct PassArgs {
+    int layer;
+    int group;
+    int ninst;
+    const int *inst;         // instance ids having this group
+    const uint64_t *prefix;  // tile prefix sums (ninst + 1)
+};
+
+template <typename R> constexpr int tile_bits();
+template <> constexpr int tile_bits<float>() { return 12; }
+template <> constexpr int tile_bits<double>() { return 11; }
+
+// Geometry of group g of an n-qubit instance for tile width T.
+struct Geo {
+    int T0;        // number of tile bits
+    int rb0;       // first rotated local bit
+    int nrot;      // number of rotated qubits (local bits rb0 .. rb0+nrot-1)
+    int q0;        // qubit of local bit rb0
+    int p0;        // global position of local bit 5 (g >= 1)
+    bool contiguous;
+};
+
+__host__ __device__ inline Geo geometry(int n, int g, int T) {
+    Geo G;
+    if (g == 0) {
+        G.T0 = n < T ? n : T;
+        G.rb0 = 0;
+        G.nrot = G.T0;
+        G.q0 = 0;
+        G.p0 = 0;
+        G.contiguous = true;
+    } else {
+        const int W = T - 5;
+        const int lo = T + (g - 1) * W, hi = (T + g * W < n) ? T + g * W : n;
+        G.nrot = hi - lo;
+        G.T0 = 5 + G.nrot;
+        G.rb0 = 5;
+        G.q0 = lo;
+        G.p0 = lo;
+        G.contiguous = false;
+    }
+    return G;
+}
+
+__host__ __device__ inline int group_count(int n, int T) {
+    if (n <= T) return 1;
+    const int W = T - 5;
+    return 1 + (n - T + W - 1) / W;
+}
+
+// global amplitude index of local index l in tile t of group geometry G
+__device__ __forceinline__ uint64_t tile_global(const Geo &G, uint64_t t, uint32_t l) {
+    if (G.contiguous) return (t << G.T0) | l;
+    // non-tile bits: 5 .. p0-1 (low part of t) and p0+nrot .. n-1 (high part)
+    const int lowbits = G.p0 - 5;
+    const uint64_t tlo = t & ((uint64_t(1) << lowbits) - 1), thi = t >> lowbits;
+    return (thi << (G.p0 + G.nrot)) | (uint64_t(l >> 5) << G.p0) | (tlo << 5) | (l & 31u);
+}
+
+__device__ __forceinline__ bool cz_ladder_odd(uint64_t x, int n) {
+    const uint64_t m = n > 1 ? ((uint64_t(1) << (n - 1)) - 1) : 0;
+    return __popcll(x & (x >> 1) & m) & 1;
+}
+
+// locate the instance of global tile index gt (binary search on the prefix)
+__device__ __forceinline__ int find_inst(const PassArgs &P, uint64_t gt) {
+    int lo = 0, hi = P.ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.prefix[mid] <= gt) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T2>
+__device__ __forceinline__ void ry(T2 &a, T2 &b, float c, float s) {
+    const T2 x = a, y = b;
+    a.x = c * x.x - s * y.x; a.y = c * x.y - s * y.y;
+    b.x = s * x.x + c * y.x; b.y = s * x.y + c * y.y;
+}
+__device__ __forceinline__ void ry(double2 &a, double2 &b, double c, double s) {
+    const double2 x = a, y = b;
+    a.x = c * x.x - s * y.x; a.y = c * x.y - s * y.y;
+    b.x = s * x.x + c * y.x; b.y = s * x.y + c * y.y;
+}
+// multiply by (cz - i sz) (bit 0) or (cz + i sz) (bit 1); sgn = -1 / +1
+template <typename T2, typename R>
+__device__ __forceinline__ void rz1(T2 &a, R cz, R sz) {
+    const T2 x = a;
+    a.x = cz * x.x + sz * x.y;
+    a.y = cz * x.y - sz * x.x;
+}
+template <typename T2, typename R>
+__device__ __forceinline__ void rz2(T2 &b, R cz, R sz) {
+    const T2 x = b;
+    b.x = cz * x.x - sz * x.y;
+    b.y = cz * x.y + sz * x.x;
+}
+
+// forward: RZ_q RY_q on the pair (a, b) of qubit q
+template <typename T2, typename R>
+__device__ __forceinline__ void fwd_pair(T2 &a, T2 &b, const Rot<R> &r) {
+    ry(a, b, r.cy, r.sy);
+    rz1(a, r.cz, r.sz);
+    rz2(b, r.cz, r.sz);
+}
+
+// apply the forward rotations of local bits bits[0..nb) (nb <= 3) to the tile
+template <typename R, int NB>
+__device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, const Rot<R> *rot) {
+    using T2 = typename Cx<R>::T;
+    const uint32_t nsub = 1u << (T0 - NB);
+    for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
+        uint32_t base = s;
+#pragma unroll
+        for (int i = 0; i < NB; i++) {  // bits ascending
+            const int b = bits[i];
+            base = ((base >> b) << (b + 1)) | (base & ((1u << b) - 1));
+        }
+        T2 v[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            uint32_t o = base;
+#pragma unroll
+            for (int i = 0; i < NB; i++)
+                if ((j >> i) & 1) o |= 1u << bits[i];
+            v[j] = tile[o];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; i++)
+#pragma unroll
+            for (int j = 0; j < (1 << NB); j++)
+                if (!((j >> i) & 1)) fwd_pair(v[j], v[j | (1 << i)], rot[i]);
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            uint32_t o = base;
+#pragma unroll
+            for (int i = 0; i < NB; i++)
+                if ((j >> i) & 1) o |= 1u << bits[i];
+            tile[o] = v[j];
+        }
+    }
+}
+
+template <typename R>
+__device__ void apply_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot<R> *rots /* per qubit of layer */) {
+    for (int r0 = 0; r0 < G.nrot; r0 += 3) {
+        const int nb = G.nrot - r0 < 3 ? G.nrot - r0 : 3;
+        int bits[3];
+        Rot<R> rr[3];
+        for (int i = 0; i < nb; i++) {
+            bits[i] = G.rb0 + r0 + i;
+            rr[i] = rots[G.q0 + r0 + i];
+        }
+        if (nb == 3) tile_round<R, 3>(tile, G.T0, bits, rr);
+        else if (nb == 2) tile_round<R, 2>(tile, G.T0, bits, rr);
+        else tile_round<R, 1>(tile, G.T0, bits, rr);
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts,
+              const Rot<R> *__restrict__ rot, const __grid_constant__ PassArgs P) {
+    using T2 = typename Cx<R>::T;
+    constexpr int T = tile_bits<R>();
+    __shared__ __align__(16) T2 tile[1 << T];
+    const uint64_t total = P.prefix[P.ninst];
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t t_begin = uint64_t(blockIdx.x) * per;
+    const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    for (uint64_t gt = t_begin; gt < t_end; gt++) {
+        const int k = find_inst(P, gt);
+        const HeaInst I = insts[P.inst[k]];
+        const Geo G = geometry(I.n, P.group, T);
+        const uint64_t t = gt - P.prefix[k];
+        T2 *sv = arena + I.off;
+        const uint32_t sz = 1u << G.T0;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) tile[l] = sv[tile_global(G, t, l)];
+        __syncthreads();
+        apply_rotations<R>(tile, G, rot + I.rot_off + size_t(P.layer) * I.n);
+        const bool last = P.group == I.ngroups - 1;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+            const uint64_t x = tile_global(G, t, l);
+            T2 v = tile[l];
+            if (last && cz_ladder_odd(x, I.n)) {
+                v.x = -v.x;
+                v.y = -v.y;
+            }
+            sv[x] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// shared-memory FP64 accumulator slots flushed to global when the instance changes
+__device__ __forceinline__ void flush_slots(double *acc, int nslots, double *dst) {
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        if (acc[i] != 0.0) atomicAdd(dst + i, acc[i]);
+        acc[i] = 0.0;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// energy contribution of one group: ZZ (group 0 only) and X_q of the group's qubits
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts,
+             const __grid_constant__ PassArgs P, double zz, double hx, double *__restrict__ energy) {
+    using T2 = typename Cx<R>::T;
+    constexpr int T = tile_bits<R>();
+    __shared__ __align__(16) T2 tile[1 << T];
+    __shared__ double slot;
+    const uint64_t total = P.prefix[P.ninst];
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t t_begin = uint64_t(blockIdx.x) * per;
+    const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    if (threadIdx.x == 0) slot = 0.0;
+    int cur = -1;
+    for (uint64_t gt = t_begin; gt < t_end; gt++) {
+        const int k = find_inst(P, gt);
+        const int id = P.inst[k];
+        if (id != cur) {
+            __syncthreads();
+            if (cur >= 0) flush_slots(&slot, 1, energy + cur);
+            __syncthreads();
+            cur = id;
+        }
+        const HeaInst I = insts[id];
+        const Geo G = geometry(I.n, P.group, T);
+        const uint64_t t = gt - P.prefix[k];
+        const T2 *sv = arena + I.off;
+        const uint32_t sz = 1u << G.T0;
+        Acc<R> acc;
+        const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+            const uint64_t x = tile_global(G, t, l);
+            const T2 v = sv[x];
+            tile[l] = v;
+            if (P.group == 0) {
+                const int odd = __popcll((x ^ (x >> 1)) & zmask);
+                acc.add(R(zz * double(I.n - 1 - 2 * odd)) * (v.x * v.x + v.y * v.y));
+            }
+        }
+        __syncthreads();
+        // <X_q> = sum_x Re(conj(psi_x) psi_{x ^ 2^q}) = 2 sum_{x_q = 0} Re(...)
+        for (int r = 0; r < G.nrot; r++) {
+            const int b = G.rb0 + r;
+            for (uint32_t p = threadIdx.x; p < (sz >> 1); p += blockDim.x) {
+                const uint32_t l0 = ((p >> b) << (b + 1)) | (p & ((1u << b) - 1));
+                const T2 a = tile[l0], c = tile[l0 | (1u << b)];
+                acc.add(R(2.0 * hx) * (a.x * c.x + a.y * c.y));
+            }
+        }
+        double v = warp_sum(acc.value());
+        if ((threadIdx.x & 31) == 0) atomicAdd(&slot, v);
+        __syncthreads();
+    }
+    __syncthreads();
+    if (cur >= 0) flush_slots(&slot, 1, energy + cur);
+}
+
+// lam = H psi for one group (group 0 writes, the others add)
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
+             const HeaInst *__restrict__ insts, const __grid_constant__ PassArgs P, double zz, double hx) {
+    using T2 = typename Cx<R>::T;
+    constexpr int T = tile_bits<R>();
+    __shared__ __align__(16) T2 tile[1 << T];
+    const uint64_t total = P.prefix[P.ninst];
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t t_begin = uint64_t(blockIdx.x) * per;
+    const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    for (uint64_t gt = t_begin; gt < t_end; gt++) {
+        const int k = find_inst(P, gt);
+        const HeaInst I = insts[P.inst[k]];
+        const Geo G = geometry(I.n, P.group, T);
+        const uint64_t t = gt - P.prefix[k];
+        const uint32_t sz = 1u << G.T0;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) tile[l] = psi[I.off + tile_global(G, t, l)];
+        __syncthreads();
+        const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+            const uint64_t x = tile_global(G, t, l);
+            T2 out;
+            out.x = 0;
+            out.y = 0;
+            if (P.group == 0) {
+                const int odd = __popcll((x ^ (x >> 1)) & zmask);
+                const R d = R(zz * double(I.n - 1 - 2 * odd));
+                out.x = d * tile[l].x;
+                out.y = d * tile[l].y;
+            } else {
+                out = lam[I.off + x];
+            }
+            for (int r = 0; r < G.nrot; r++) {
+                const T2 nb = tile[l ^ (1u << (G.rb0 + r))];
+                out.x += R(hx) * nb.x;
+                out.y += R(hx) * nb.y;
+            }
+            lam[I.off + x] = out;
+        }
+        __syncthreads();
+    }
+}
+
+// backward sweep of one (layer, group) on psi and lam, with gradients
+template <typename R, int NB>
+__device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, const int *bits, const Rot<R> *rot,
+                          Acc<R> (&gz)[3], Acc<R> (&gy)[3]) {
+    using T2 = typename Cx<R>::T;
+    const uint32_t nsub = 1u << (T0 - NB);
+    for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
+        uint32_t base = s;
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            const int b = bits[i];
+            base = ((base >> b) << (b + 1)) | (base & ((1u << b) - 1));
+        }
+        T2 p[1 << NB], l[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            uint32_t o = base;
+#pragma unroll
+            for (int i = 0; i < NB; i++)
+                if ((j >> i) & 1) o |= 1u << bits[i];
+            p[j] = tp[o];
+            l[j] = tl[o];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            const Rot<R> r = rot[i];
+#pragma unroll
+            for (int j = 0; j < (1 << NB); j++) {
+                if ((j >> i) & 1) continue;
+                T2 &p0 = p[j], &p1 = p[j | (1 << i)], &l0 = l[j], &l1 = l[j | (1 << i)];
+                // dE/dphi = Im<lam|Z|psi> = Im(conj(l0) p0) - Im(conj(l1) p1)
+                gz[i].add((l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x));
+                // un-apply RZ: multiply by (cz + i sz) on bit 0, (cz - i sz) on bit 1
+                rz2(p0, r.cz, r.sz); rz1(p1, r.cz, r.sz);
+                rz2(l0, r.cz, r.sz); rz1(l1, r.cz, r.sz);
+                // dE/dtheta = Im<lam|Y|psi>; Y psi = (-i p1, i p0)
+                //   Im(conj(l0)(-i p1)) = -(l0.x p1.x + l0.y p1.y); Im(conj(l1)(i p0)) = l1.x p0.x + l1.y p0.y
+                gy[i].add((l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y));
+                // un-apply RY: RY(-theta)
+                ry(p0, p1, r.cy, -r.sy);
+                ry(l0, l1, r.cy, -r.sy);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            uint32_t o = base;
+#pragma unroll
+            for (int i = 0; i < NB; i++)
+                if ((j >> i) & 1) o |= 1u << bits[i];
+            tp[o] = p[j];
+            tl[o] = l[j];
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
+               const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
+               const __grid_constant__ PassArgs P, double *__restrict__ grad) {
+    using T2 = typename Cx<R>::T;
+    constexpr int T = tile_bits<R>();
+    extern __shared__ __align__(16) unsigned char hea_smem[];  // psi tile, lam tile (64 KB)
+    T2 *tp = reinterpret_cast<T2 *>(hea_smem);
+    T2 *tl = tp + (1 << T);
+    __shared__ double gacc[2 * T];  // [RY of each rotated qubit][RZ of each]
+    const uint64_t total = P.prefix[P.ninst];
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t t_begin = uint64_t(blockIdx.x) * per;
+    const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) gacc[i] = 0.0;
+    int cur = -1, cur_n = 0, cur_q0 = 0, cur_nrot = 0;
+    int cur_poff = 0;
+    auto flush = [&]() {
+        // gacc[r] -> RY of qubit q0 + r, gacc[T + r] -> RZ of qubit q0 + r
+        for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) {
+            const int r = i % T;
+            if (r < cur_nrot && gacc[i] != 0.0) {
+                const int q = cur_q0 + r;
+                const int p = cur_poff + 2 * cur_n * P.layer + (i < T ? q : cur_n + q);
+                atomicAdd(grad + p, gacc[i]);
+            }
+            gacc[i] = 0.0;
+        }
+    };
+    __syncthreads();
+    for (uint64_t gt = t_begin; gt < t_end; gt++) {
+        const int k = find_inst(P, gt);
+        const int id = P.inst[k];
+        const HeaInst I = insts[id];
+        const Geo G = geometry(I.n, P.group, T);
+        if (id != cur) {
+            __syncthreads();
+            if (cur >= 0) flush();
+            __syncthreads();
+            cur = id;
+            cur_n = I.n;
+            cur_q0 = G.q0;
+            cur_nrot = G.nrot;
+            cur_poff = I.param_off;
+        }
+        const uint64_t t = gt - P.prefix[k];
+        const uint32_t sz = 1u << G.T0;
+        const bool last = P.group == I.ngroups - 1;
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+            const uint64_t x = tile_global(G, t, l);
+            T2 a = psi[I.off + x], b = lam[I.off + x];
+            if (last && cz_ladder_odd(x, I.n)) {  // undo the CZ ladder (self-inverse)
+                a.x = -a.x; a.y = -a.y;
+                b.x = -b.x; b.y = -b.y;
+            }
+            tp[l] = a;
+            tl[l] = b;
+        }
+        __syncthreads();
+        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
+        for (int r0 = 0; r0 < G.nrot; r0 += 3) {
+            const int nb = G.nrot - r0 < 3 ? G.nrot - r0 : 3;
+            int bits[3];
+            Rot<R> rr[3];
+            for (int i = 0; i < nb; i++) {
+                bits[i] = G.rb0 + r0 + i;
+                rr[i] = lr[G.q0 + r0 + i];
+            }
+            Acc<R> gz[3], gy[3];
+            if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gz, gy);
+            else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gz, gy);
+            else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gz, gy);
+            for (int i = 0; i < nb; i++) {
+                const double vz = warp_sum(gz[i].value()), vy = warp_sum(gy[i].value());
+                if ((threadIdx.x & 31) == 0) {
+                    atomicAdd(&gacc[T + r0 + i], vz);
+                    atomicAdd(&gacc[r0 + i], vy);
+                }
+            }
+            __syncthreads();
+        }
+        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+            const uint64_t x = tile_global(G, t, l);
+            psi[I.off + x] = tp[l];
+            lam[I.off + x] = tl[l];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (cur >= 0) flush();
+}
+
+// rotation table from the parameters: rot[inst][layer][q]
+template <typename R>
+__global__ void k_hea_prep(const HeaInst *__restrict__ insts, int ninst, int layers,
+                           const double *__restrict__ params, Rot<R> *__restrict__ rot) {
+    const int id = blockIdx.x;
+    if (id >= ninst) return;
+    const HeaInst I = insts[id];
+    for (int e = threadIdx.x; e < layers * I.n; e += blockDim.x) {
+        const int l = e / I.n, q = e % I.n;
+        const double th = params[I.param_off + 2 * I.n * l + q];
+        const double ph = params[I.param_off + 2 * I.n * l + I.n + q];
+        Rot<R> r;
+        r.cy = R(cos(0.5 * th));
+        r.sy = R(sin(0.5 * th));
+        r.cz = R(cos(0.5 * ph));
+        r.sz = R(sin(0.5 * ph));
+        rot[I.rot_off + e] = r;
+    }
+}
+
+// every instance to |0...0>
+template <typename R>
+__global__ void k_hea_reset(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts, int ninst) {
+    const int id = blockIdx.y;
+    if (id >= ninst) return;
+    const HeaInst I = insts[id];
+    using T2 = typename Cx<R>::T;
+    const uint64_t N = uint64_t(1) << I.n;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += uint64_t(gridDim.x) * blockDim.x) {
+        T2 v;
+        v.x = i == 0 ? R(1) : R(0);
+        v.y = 0;
+        arena[I.off + i] = v;
+    }
+}
+
+}  // namespace
+}  // namespace cast
+
+// ------------------------------------------------------------------- host
+struct cast_hea {
+    int ninst = 0, layers = 0, nparams = 0;
+    cast_dtype dt = CAST_C64;
+    bool with_grad = false;
+    cudaStream_t stream = nullptr;
+    std::vector<cast::HeaInst> inst;
+    void *psi = nullptr, *lam = nullptr;  // arenas
+    cast::HeaInst *d_inst = nullptr;
+    void *d_rot = nullptr;
+    double *d_params = nullptr, *d_out = nullptr;  // out: [ninst energies][nparams grads]
+    double *h_params = nullptr, *h_out = nullptr;  // pinned
+    int *d_pass_inst = nullptr;
+    uint64_t *d_pass_prefix = nullptr;
+    std::vector<int> pass_ninst;            // per group
+    std::vector<size_t> pass_inst_off, pass_prefix_off;
+    std::vector<uint64_t> pass_tiles;
+    int ngroups_max = 0;
+    double zz = 0, hx = 0;
+    cudaGraph_t graph[2] = {nullptr, nullptr};  // [energy][grad]
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    double graph_zz[2] = {0, 0}, graph_hx[2] = {0, 0};
+    int grid = 0;
+};
+
+namespace cast {
+namespace {
+
+template <typename R>
+cast_status queue_hea(cast_hea *b, bool grad) {
+    using T2 = typename Cx<R>::T;
+    constexpr int T = tile_bits<R>();
+    cudaStream_t st = b->stream;
+    T2 *psi = static_cast<T2 *>(b->psi), *lam = static_cast<T2 *>(b->lam);
+    Rot<R> *rot = static_cast<Rot<R> *>(b->d_rot);
+    const int G = b->grid;
+    auto pass = [&](int layer, int g) {
+        PassArgs P;
+        P.layer = layer;
+        P.group = g;
+        P.ninst = b->pass_ninst[g];
+        P.inst = b->d_pass_inst + b->pass_inst_off[g];
+        P.prefix = b->d_pass_prefix + b->pass_prefix_off[g];
+        return P;
+    };
+    CAST_CUDA(cudaMemcpyAsync(b->d_params, b->h_params, sizeof(double) * b->nparams, cudaMemcpyHostToDevice, st));
+    CAST_CUDA(cudaMemsetAsync(b->d_out, 0, sizeof(double) * (b->ninst + (grad ? b->nparams : 0)), st));
+    k_hea_prep<R><<<b->ninst, 256, 0, st>>>(b->d_inst, b->ninst, b->layers, b->d_params, rot);
+    k_hea_reset<R><<<dim3(64, b->ninst), 256, 0, st>>>(psi, b->d_inst, b->ninst);
+    for (int l = 0; l < b->layers; l++)
+        for (int g = 0; g < b->ngroups_max; g++) {
+            if (b->pass_ninst[g] == 0) continue;
+            ProfScope ps(st, std::string("hea_fwd_") + dt_name(b->dt), 2.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
+            k_hea_forward<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, rot, pass(l, g));
+        }
+    for (int g = 0; g < b->ngroups_max; g++) {
+        if (b->pass_ninst[g] == 0) continue;
+        ProfScope ps(st, std::string("hea_energy_") + dt_name(b->dt), sizeof(T2) * double(b->pass_tiles[g] << T), 0);
+        k_hea_energy<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
+    }
+    if (grad) {
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(2 * sizeof(T2) << T)));
+        for (int g = 0; g < b->ngroups_max; g++) {
+            if (b->pass_ninst[g] == 0) continue;
+            k_hea_lambda<R><<<G, kThreads, 0, st>>>(psi, lam, b->d_inst, pass(0, g), b->zz, b->hx);
+        }
+        for (int l = b->layers - 1; l >= 0; l--)
+            for (int g = b->ngroups_max - 1; g >= 0; g--) {
+                if (b->pass_ninst[g] == 0) continue;
+                ProfScope ps(st, std::string("hea_bwd_") + dt_name(b->dt),
+                             4.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
+                k_hea_backward<R><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(psi, lam, b->d_inst, rot, pass(l, g),
+                                                                          b->d_out + b->ninst);
+            }
+    }
+    CAST_CUDA(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * (b->ninst + (grad ? b->nparams : 0)),
+                              cudaMemcpyDeviceToHost, st));
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
+void free_hea(cast_hea *b) {
+    for (int i = 0; i < 2; i++) {
+        if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+        if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+    }
+    cudaFree(b->psi);
+    cudaFree(b->lam);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_rot);
+    cudaFree(b->d_params);
+    cudaFree(b->d_out);
+    cudaFree(b->d_pass_inst);
+    cudaFree(b->d_pass_prefix);
+    cudaFreeHost(b->h_params);
+    cudaFreeHost(b->h_out);
+    delete b;
+}
+
+}  // namespace
+}  // namespace cast
+
+using namespace cast;
+
+extern "C" {
+
+cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers, cast_dtype dt, int with_grad,
+                            void *cuda_stream, cast_hea **out) {
+    if (!out) return fail(CAST_ERR_ARG, "null output handle");
+    *out = nullptr;
+    if (n_instances < 1 || !n_qubits) return fail(CAST_ERR_ARG, "need at least one instance");
+    if (layers < 1) return fail(CAST_ERR_ARG, "layers must be >= 1");
+    if (dt != CAST_C64 && dt != CAST_C128) return fail(CAST_ERR_ARG, "unknown dtype");
+    const int T = dt == CAST_C64 ? tile_bits<float>() : tile_bits<double>();
+    cast_hea *b = new cast_hea();
+    b->ninst = n_instances;
+    b->layers = layers;
+    b->dt = dt;
+    b->with_grad = with_grad != 0;
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t S = amp_bytes(dt);
+    uint64_t off = 0;
+    int poff = 0, roff = 0;
+    for (int i = 0; i < n_instances; i++) {
+        const int n = n_qubits[i];
+        if (n < 2 || n > 30) {
+            delete b;
+            return fail(CAST_ERR_ARG, "instance qubit counts must be in 2..30");
+        }
+        HeaInst I;
+        I.off = off;
+        I.n = n;
+        I.ngroups = group_count(n, T);
+        I.param_off = poff;
+        I.rot_off = roff;
+        b->inst.push_back(I);
+        off += (uint64_t(1) << n) + (256 / S);  // keep every state 256-byte aligned
+        off = (off + 255) & ~uint64_t(255);
+        poff += 2 * n * layers;
+        roff += n * layers;
+        b->ngroups_max = std::max(b->ngroups_max, I.ngroups);
+    }
+    if (b->ngroups_max > kMaxGroups) {
+        delete b;
+        return fail(CAST_ERR_UNSUPPORTED, "too many qubit groups");
+    }
+    b->nparams = poff;
+    // per-group instance lists and tile prefix sums
+    std::vector<int> all_inst;
+    std::vector<uint64_t> all_prefix;
+    b->pass_ninst.assign(b->ngroups_max, 0);
+    b->pass_tiles.assign(b->ngroups_max, 0);
+    for (int g = 0; g < b->ngroups_max; g++) {
+        b->pass_inst_off.push_back(all_inst.size());
+        b->pass_prefix_off.push_back(all_prefix.size());
+        uint64_t acc = 0;
+        for (int i = 0; i < n_instances; i++) {
+            if (g >= b->inst[i].ngroups) continue;
+            const Geo Gm = geometry(b->inst[i].n, g, T);
+            all_inst.push_back(i);
+            all_prefix.push_back(acc);
+            acc += uint64_t(1) << (b->inst[i].n - Gm.T0);
+            b->pass_ninst[g]++;
+        }
+        all_prefix.push_back(acc);
+        b->pass_tiles[g] = acc;
+    }
+    const size_t rot_bytes = (dt == CAST_C64 ? sizeof(Rot<float>) : sizeof(Rot<double>)) * size_t(roff);
+    bool ok = cudaMalloc(&b->psi, off * S) == cudaSuccess;
+    ok = ok && (!b->with_grad || cudaMalloc(&b->lam, off * S) == cudaSuccess);
+    ok = ok && cudaMalloc(&b->d_inst, sizeof(HeaInst) * n_instances) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_rot, rot_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_params, sizeof(double) * b->nparams) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_out, sizeof(double) * (n_instances + b->nparams)) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_pass_inst, sizeof(int) * all_inst.size()) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_pass_prefix, sizeof(uint64_t) * all_prefix.size()) == cudaSuccess;
+    ok = ok && cudaMallocHost(&b->h_params, sizeof(double) * b->nparams) == cudaSuccess;
+    ok = ok && cudaMallocHost(&b->h_out, sizeof(double) * (n_instances + b->nparams)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_hea(b);
+        return fail(CAST_ERR_OOM, "batch allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(HeaInst) * n_instances, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pass_inst, all_inst.data(), sizeof(int) * all_inst.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pass_prefix, all_prefix.data(), sizeof(uint64_t) * all_prefix.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_hea(b);
+        return cuda_fail(e, "batch upload");
+    }
+    b->grid = sm_count_cached() * (dt == CAST_C64 ? 6 : 6);
+    *out = b;
+    return CAST_OK;
+}
+
+static cast_status run_hea(cast_hea *b, const double *params, double zz, double hx, double *energies,
+                           double *grads, bool grad) {
+    if (!b || !params || !energies || (grad && !grads)) return fail(CAST_ERR_ARG, "null argument");
+    if (grad && !b->with_grad) return fail(CAST_ERR_ARG, "batch was created without gradient buffers");
+    if (!std::isfinite(zz) || !std::isfinite(hx)) return fail(CAST_ERR_ARG, "non-finite coefficient");
+    for (int p = 0; p < b->nparams; p++)
+        if (!std::isfinite(params[p])) return fail(CAST_ERR_ARG, "non-finite parameter");
+    const int gi = grad ? 1 : 0;
+    CAST_CUDA(cudaStreamSynchronize(b->stream));  // the pinned buffers are free
+    std::memcpy(b->h_params, params, sizeof(double) * b->nparams);
+    b->zz = zz;
+    b->hx = hx;
+    // the graph bakes in zz and hx; rebuild it when they change
+    if (b->exec[gi] && (b->graph_zz[gi] != zz || b->graph_hx[gi] != hx)) {
+        cudaGraphExecDestroy(b->exec[gi]);
+        cudaGraphDestroy(b->graph[gi]);
+        b->exec[gi] = nullptr;
+        b->graph[gi] = nullptr;
+    }
+    if (!b->exec[gi]) {
+        cudaStream_t cap = nullptr;
+        CAST_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaStream_t orig = b->stream;
+        b->stream = cap;
+        cast_status st = CAST_OK;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "cudaStreamBeginCapture");
+        } else {
+            st = b->dt == CAST_C64 ? queue_hea<float>(b, grad) : queue_hea<double>(b, grad);
+            cudaGraph_t gph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cap, &gph);
+            if (st == CAST_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
+            if (st == CAST_OK) {
+                e = cudaGraphInstantiate(&b->exec[gi], gph, 0);
+                if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate");
+                b->graph[gi] = gph;
+                b->graph_zz[gi] = zz;
+                b->graph_hx[gi] = hx;
+            } else if (gph) {
+                cudaGraphDestroy(gph);
+            }
+        }
+        b->stream = orig;
+        cudaStreamDestroy(cap);
+        if (st != CAST_OK) return st;
+    }
+    CAST_CUDA(cudaGraphLaunch(b->exec[gi], b->stream));
+    CAST_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->ninst; i++) energies[i] = b->h_out[i];
+    if (grad)
+        for (int p = 0; p < b->nparams; p++) grads[p] = b->h_out[b->ninst + p];
+    return take_device_error();
+}
+
+cast_status cast_hea_energy(cast_hea *b, const double *params, double zz, double hx, double *energies) {
+    return run_hea(b, params, zz, hx, energies, nullptr, false);
+}
+
+cast_status cast_hea_grad(cast_hea *b, const double *params, double zz, double hx, double *energies,
+                          double *grads) {
+    return run_hea(b, params, zz, hx, energies, grads, true);
+}
+
+cast_status cast_hea_info(const cast_hea *b, int *n_params, int *n_passes_per_layer_max) {
+    if (!b) return fail(CAST_ERR_ARG, "null batch");
+    if (n_params) *n_params = b->nparams;
+    if (n_passes_per_layer_max) *n_passes_per_layer_max = b->ngroups_max;
+    return CAST_OK;
+}
+
+cast_status cast_hea_destroy(cast_hea *b) {
+    if (!b) return CAST_OK;
+    cudaStreamSynchronize(b->stream);
+    free_hea(b);
+    return CAST_OK;
+}
+
+}  // extern "C"

@@ -36,6 +36,8 @@ cudaEvent_t take_event() {
 
 ProfScope::ProfScope(cudaStream_t s, const std::string &family, double bytes, double flops) {
     if (!g_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_mu);
     cudaEvent_t a = take_event(), b = take_event();
     if (!a || !b) return;
