@@ -229,8 +229,36 @@ __device__ void apply_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot
     }
 }
 
+// A thread's share of one tile: IT = 2^T / 256 amplitudes, loaded together so
+// that all of them are in flight at once.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+struct TileRegs {
+    static constexpr int IT = (1 << tile_bits<R>()) / kThreads;
+    typename Cx<R>::T v[IT];
+};
+
+template <typename R>
+__device__ __forceinline__ void tile_load(TileRegs<R> &b, const typename Cx<R>::T *__restrict__ sv, const Geo &G,
+                                          uint64_t t) {
+    const uint32_t sz = 1u << G.T0;
+#pragma unroll
+    for (int i = 0; i < TileRegs<R>::IT; i++) {
+        const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
+        if (l < sz) b.v[i] = sv[tile_global(G, t, l)];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename Cx<R>::T *tile, uint32_t sz) {
+#pragma unroll
+    for (int i = 0; i < TileRegs<R>::IT; i++) {
+        const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
+        if (l < sz) tile[l] = b.v[i];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts,
               const Rot<R> *__restrict__ rot, const __grid_constant__ PassArgs P) {
     using T2 = typename Cx<R>::T;
@@ -240,21 +268,35 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    if (t_begin >= t_end) return;
+    // the next tile's loads are issued before this tile's rotations run
+    TileRegs<R> buf;
+    int k = find_inst(P, t_begin);
+    HeaInst I = insts[P.inst[k]];
+    Geo G = geometry(I.n, P.group, T);
+    uint64_t t = t_begin - P.prefix[k];
+    tile_load<R>(buf, arena + I.off, G, t);
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
-        const int k = find_inst(P, gt);
-        const HeaInst I = insts[P.inst[k]];
-        const Geo G = geometry(I.n, P.group, T);
-        const uint64_t t = gt - P.prefix[k];
-        T2 *sv = arena + I.off;
         const uint32_t sz = 1u << G.T0;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) tile[l] = sv[tile_global(G, t, l)];
+        tile_put<R>(buf, tile, sz);
         __syncthreads();
-        apply_rotations<R>(tile, G, rot + I.rot_off + size_t(P.layer) * I.n);
-        const bool last = P.group == I.ngroups - 1;
+        const HeaInst Ic = I;
+        const Geo Gc = G;
+        const uint64_t tc = t;
+        if (gt + 1 < t_end) {
+            k = find_inst(P, gt + 1);
+            I = insts[P.inst[k]];
+            G = geometry(I.n, P.group, T);
+            t = gt + 1 - P.prefix[k];
+            tile_load<R>(buf, arena + I.off, G, t);
+        }
+        apply_rotations<R>(tile, Gc, rot + Ic.rot_off + size_t(P.layer) * Ic.n);
+        const bool last = P.group == Ic.ngroups - 1;
+        T2 *sv = arena + Ic.off;
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(G, t, l);
+            const uint64_t x = tile_global(Gc, tc, l);
             T2 v = tile[l];
-            if (last && cz_ladder_odd(x, I.n)) {
+            if (last && cz_ladder_odd(x, Ic.n)) {
                 v.x = -v.x;
                 v.y = -v.y;
             }
@@ -309,13 +351,19 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
         const uint32_t sz = 1u << G.T0;
         Acc<R> acc;
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(G, t, l);
-            const T2 v = sv[x];
-            tile[l] = v;
-            if (P.group == 0) {
+        TileRegs<R> buf;
+        tile_load<R>(buf, sv, G, t);
+        tile_put<R>(buf, tile, sz);
+        if (P.group == 0) {
+            const R zzr = R(zz);
+#pragma unroll
+            for (int i = 0; i < TileRegs<R>::IT; i++) {
+                const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
+                if (l >= sz) continue;
+                const uint64_t x = tile_global(G, t, l);
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
-                acc.add(R(zz * double(I.n - 1 - 2 * odd)) * (v.x * v.x + v.y * v.y));
+                const T2 v = buf.v[i];
+                acc.add(zzr * R(I.n - 1 - 2 * odd) * (v.x * v.x + v.y * v.y));
             }
         }
         __syncthreads();
@@ -354,7 +402,11 @@ k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__res
         const Geo G = geometry(I.n, P.group, T);
         const uint64_t t = gt - P.prefix[k];
         const uint32_t sz = 1u << G.T0;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) tile[l] = psi[I.off + tile_global(G, t, l)];
+        {
+            TileRegs<R> buf;
+            tile_load<R>(buf, psi + I.off, G, t);
+            tile_put<R>(buf, tile, sz);
+        }
         __syncthreads();
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
@@ -407,22 +459,25 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             const Rot<R> r = rot[i];
+            R sz = 0, sy = 0;  // this sub-slice's share, added to the compensated sums once
 #pragma unroll
             for (int j = 0; j < (1 << NB); j++) {
                 if ((j >> i) & 1) continue;
                 T2 &p0 = p[j], &p1 = p[j | (1 << i)], &l0 = l[j], &l1 = l[j | (1 << i)];
                 // dE/dphi = Im<lam|Z|psi> = Im(conj(l0) p0) - Im(conj(l1) p1)
-                gz[i].add((l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x));
+                sz += (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
                 // un-apply RZ: multiply by (cz + i sz) on bit 0, (cz - i sz) on bit 1
                 rz2(p0, r.cz, r.sz); rz1(p1, r.cz, r.sz);
                 rz2(l0, r.cz, r.sz); rz1(l1, r.cz, r.sz);
                 // dE/dtheta = Im<lam|Y|psi>; Y psi = (-i p1, i p0)
                 //   Im(conj(l0)(-i p1)) = -(l0.x p1.x + l0.y p1.y); Im(conj(l1)(i p0)) = l1.x p0.x + l1.y p0.y
-                gy[i].add((l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y));
+                sy += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
                 // un-apply RY: RY(-theta)
                 ry(p0, p1, r.cy, -r.sy);
                 ry(l0, l1, r.cy, -r.sy);
             }
+            gz[i].add(sz);
+            gy[i].add(sy);
         }
 #pragma unroll
         for (int j = 0; j < (1 << NB); j++) {
@@ -437,7 +492,7 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
 k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
                const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
                const __grid_constant__ PassArgs P, double *__restrict__ grad) {
@@ -485,15 +540,21 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
         const uint64_t t = gt - P.prefix[k];
         const uint32_t sz = 1u << G.T0;
         const bool last = P.group == I.ngroups - 1;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(G, t, l);
-            T2 a = psi[I.off + x], b = lam[I.off + x];
-            if (last && cz_ladder_odd(x, I.n)) {  // undo the CZ ladder (self-inverse)
-                a.x = -a.x; a.y = -a.y;
-                b.x = -b.x; b.y = -b.y;
+        for (int v = 0; v < 2; v++) {  // psi, then lam: one register buffer live at a time
+            TileRegs<R> bb;
+            tile_load<R>(bb, (v == 0 ? psi : lam) + I.off, G, t);
+            T2 *dst = v == 0 ? tp : tl;
+#pragma unroll
+            for (int i = 0; i < TileRegs<R>::IT; i++) {
+                const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
+                if (l >= sz) continue;
+                T2 a = bb.v[i];
+                if (last && cz_ladder_odd(tile_global(G, t, l), I.n)) {  // undo the CZ ladder (self-inverse)
+                    a.x = -a.x;
+                    a.y = -a.y;
+                }
+                dst[l] = a;
             }
-            tp[l] = a;
-            tl[l] = b;
         }
         __syncthreads();
         const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
