@@ -110,6 +110,20 @@ cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double 
 cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 
+/* Arithmetic for complex128 gates (process-wide setting):
+ *   CAST_F64_EMULATED (default): dense (k <= 5), diagonal and phased
+ *     monomial gates in double-float arithmetic on the FP32 pipe (pairs of
+ *     floats, error-free TwoSum / TwoProduct, ~2^-46 relative error), with the
+ *     FP64 <-> float-pair conversions done by integer bit manipulation;
+ *     magnitudes must stay below 2^120;
+ *   CAST_F64_NATIVE: IEEE FP64 on the FP64 pipe (about 1/67 of the FP32 rate
+ *     on this GPU).
+ * CAST_ERR_ARG for an unknown mode. */
+#define CAST_F64_EMULATED 0
+#define CAST_F64_NATIVE 1
+cast_status cast_set_f64_mode(int mode);
+int cast_get_f64_mode(void);
+
 /* ------------------------------------------------------------------------
  * Circuits and gate fusion (Section IV)
  * ---------------------------------------------------------------------- */
@@ -160,7 +174,8 @@ typedef struct {
     double zero_tol;       /* |real scalar| <= zero_tol counts as zero, default 1e-12 */
     int32_t amp_ops_per_pass; /* adaptive cost model: operations per amplitude that take as
                                  long as one pass over the state; 0 = measured default for
-                                 the state type (complex64: 82, complex128: 2) */
+                                 the state type (complex64: 82; complex128: 16 with
+                                 double-float arithmetic, 2 with native FP64) */
 } cast_options;
 
 /* Fill *o with the defaults listed above. */

@@ -64,7 +64,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
            "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
            "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode",
-           "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy")
+           "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
+           "cast_set_f64_mode", "cast_get_f64_mode")
 
 _lib = None
 
@@ -115,6 +116,8 @@ def load(build_if_missing=True):
         "cast_hea_grad": (I, [P, P, D, D, P, P]),
         "cast_hea_info": (I, [P, P, P]),
         "cast_hea_destroy": (I, [P]),
+        "cast_set_f64_mode": (I, [I]),
+        "cast_get_f64_mode": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -369,6 +372,15 @@ def cast_adjoint_grad(psi, lam, n, gates, params, terms):
 
 
 CAST_TC_OFF, CAST_TC_TF32X3 = 0, 1
+CAST_F64_EMULATED, CAST_F64_NATIVE = 0, 1
+
+
+def cast_set_f64_mode(mode):
+    _check(load().cast_set_f64_mode(int(mode)))
+
+
+def cast_get_f64_mode():
+    return int(load().cast_get_f64_mode())
 
 
 def cast_set_tensor_mode(mode):

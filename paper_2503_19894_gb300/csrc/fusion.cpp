@@ -232,7 +232,13 @@ struct Fuser {
 
 }  // namespace
 
-int64_t default_amp_ops_per_pass(cast_dtype dt) { return dt == CAST_C64 ? 82 : 2; }
+// Operations per amplitude that take as long as one pass over the state:
+// complex64 FP32 FMA 82; complex128 on double-float ~16 (each FMA costs about
+// ten FP32 instructions), on the FP64 pipe 2 (measured rates on GB300).
+int64_t default_amp_ops_per_pass(cast_dtype dt) {
+    if (dt == CAST_C64) return 82;
+    return f64_mode() == CAST_F64_EMULATED ? 16 : 2;
+}
 
 cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast_options *opt,
                          std::vector<FusedGate> *out) {

@@ -140,6 +140,10 @@ cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
+// Double-float path for complex128 gates (apply_df.cu).
+bool df_eligible(const cast_sv *sv, const PreparedGate &g);
+cast_status launch_gate_df(cast_sv *sv, const PreparedGate &g);
+int f64_mode();
 // CAST_ERR_TIMEOUT (and clears the flag) if a kernel's bounded wait gave up.
 cast_status take_device_error();
 // Queue sum_t coeff_t <psi|P_t|psi> terms sharing one x_mask; partial sums

@@ -337,3 +337,60 @@ def test_many_large_gates_wrap_the_matrix_ring(dtype, k, tensor_mode):
     got = sv.to_numpy().astype(np.complex128)
     assert np.max(np.abs(got - ref)) <= TOL[dtype] * (10 if dtype == "c64" else 1)
     sv.close()
+
+
+# ------------------------------------------------- complex128 arithmetic modes
+
+@pytest.fixture
+def f64_mode():
+    old = capi.cast_get_f64_mode()
+    yield capi
+    capi.cast_set_f64_mode(old)
+
+
+@pytest.mark.parametrize("mode", ["emulated", "native"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_complex128_modes_match_oracle(mode, k, f64_mode):
+    capi.cast_set_f64_mode(capi.CAST_F64_EMULATED if mode == "emulated" else capi.CAST_F64_NATIVE)
+    rng = np.random.default_rng(900 + k)
+    n = 13
+    psi0 = W.random_state(n, 11)
+    for placement in ("low", "high", "mixed"):
+        qs = W.sweep_targets(n, k, placement, rng)
+        for m in (W.haar_unitary(k, rng), random_diag(k, rng), random_monomial(k, rng)):
+            got = run_gate(n, "c128", psi0, qs, m)
+            assert np.max(np.abs(got - oracle_gate(psi0, "c128", qs, m))) <= 1e-12
+
+
+def test_double_float_special_values(f64_mode):
+    """Zeros, signed zeros, tiny and wide-ranging magnitudes survive the
+    integer split / join of the double-float path within 1e-12 (absolute)."""
+    capi.cast_set_f64_mode(capi.CAST_F64_EMULATED)
+    n = 10
+    rng = np.random.default_rng(4)
+    mags = 10.0 ** rng.uniform(-40, 0, 1 << n)
+    psi0 = mags * np.exp(2j * np.pi * rng.uniform(size=1 << n))
+    psi0[:8] = [0, -0.0, 1e-300, -1e-300, 1.0, -1.0, 1j, -1j]
+    psi0 = psi0 / np.linalg.norm(psi0)
+    for k in (1, 3, 5):
+        qs = W.sweep_targets(n, k, "mixed", rng)
+        u = W.haar_unitary(k, rng)
+        got = run_gate(n, "c128", psi0, qs, u)
+        ref = oracle.apply_gate(psi0.copy(), qs, u)
+        assert np.max(np.abs(got - ref)) <= 1e-12
+        # relative accuracy on the larger outputs is near 2^-44
+        big = np.abs(ref) > 1e-6
+        assert np.max(np.abs(got[big] - ref[big]) / np.abs(ref[big])) <= 1e-11
+
+
+def test_double_float_norm_stable_over_many_gates(f64_mode):
+    capi.cast_set_f64_mode(capi.CAST_F64_EMULATED)
+    n = 14
+    rng = np.random.default_rng(6)
+    gates = [W.Gate("U", W.sweep_targets(n, 4, "mixed", rng), matrix=W.haar_unitary(4, rng)) for _ in range(200)]
+    sv = pkg.StateVector(n, "c128")
+    sv.apply_circuit(gates, fusion="none")
+    assert abs(sv.expectation([W.PauliTerm(1.0, "", ())]) - 1.0) < 1e-12
+    ref = oracle.simulate(n, gates)
+    assert np.max(np.abs(sv.to_numpy() - ref)) <= 1e-12
+    sv.close()
