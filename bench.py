@@ -187,6 +187,19 @@ def roofline(profile, mp, src, launches_per_step_kind="sustained"):
     return r
 
 
+def aggregate(ms_local, step_bytes, steps, world, device="cpu"):
+    """Slowest rank's time (all-reduce MAX) and the whole-job throughput:
+    every rank processed step_bytes per step, so value = all ranks' bytes /
+    the slowest rank's time (replicas: weak scaling)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, step_bytes * steps * world / (ms_max / 1e3) / 1e9
+
+
 def _time(fn, reps):
     import torch
     fn()
@@ -368,12 +381,7 @@ def main():
         e1.record(stream)
         barrier()
         prof = capi.cast_profile_end()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = step_bytes * a.steps * world / (ms_max / 1e3) / 1e9
+    ms_max, value = aggregate(e0.elapsed_time(e1), step_bytes, a.steps, world, device="cuda")
     launches = sum(p["launches"] for p in prof)
 
     e2e = None
