@@ -166,6 +166,17 @@ typedef enum {
     CAST_FUSE_ADAPTIVE = 2  /* size test plus the cost-model test (Section IV-C) */
 } cast_fusion_mode;
 
+/* Measured cost of one gate per size and class on a state of n_qubits
+ * qubits: the GPU counterpart of the paper's CostModel (Section IV-C), which
+ * records gate times for varying size and sparsity and launch shapes.
+ * class index: 0 identity, 1 diagonal, 2 monomial, 3 dense. */
+typedef struct {
+    int32_t n_qubits;
+    int32_t dtype;                                 /* cast_dtype */
+    double ms[CAST_MAX_K + 1][4];                  /* average ms per gate; 0 = not measured */
+    int32_t blocks_per_sm[CAST_MAX_K + 1][4];      /* best CUDA-core launch width, 0 = default */
+} cast_cost_table;
+
 typedef struct {
     int32_t fusion;        /* cast_fusion_mode, default CAST_FUSE_ADAPTIVE */
     int32_t max_k;         /* largest fused gate, 1..CAST_MAX_K, default 5 */
@@ -176,7 +187,21 @@ typedef struct {
                                  long as one pass over the state; 0 = measured default for
                                  the state type (complex64: 82; complex128: 16 with
                                  double-float arithmetic, 2 with native FP64) */
+    const cast_cost_table *cost; /* adaptive: estimate a block by the measured time of its
+                                    (size, class) instead of the operation-count model;
+                                    with max_k = 0 the plan also picks the fusion width
+                                    2..CAST_MAX_K of least estimated time.  NULL = model */
 } cast_options;
+
+/* Measure the cost table on a scratch state of n_qubits (allocated and
+ * freed here) on cuda_stream: one gate of every size 1..CAST_MAX_K and class
+ * (diagonal, monomial, dense), for the CUDA-core kernels at launch widths of
+ * 1, 2, 4 and 8 blocks per SM keeping the fastest.  Waits for the results. */
+cast_status cast_autotune(cast_dtype dt, int n_qubits, void *cuda_stream, cast_cost_table *out);
+
+/* Use a table's launch widths for every later launch in this process (per
+ * state type; NULL restores the built-in widths for both types). */
+cast_status cast_set_cost_table(const cast_cost_table *t);
 
 /* Fill *o with the defaults listed above. */
 void cast_options_default(cast_options *o);

@@ -60,6 +60,33 @@ def opcount(m, zero_tol):
     return 2 * int(np.sum(np.abs(m.real) > zero_tol) + np.sum(np.abs(m.imag) > zero_tol))
 
 
+IDENTITY, DIAGONAL, MONOMIAL, DENSE = 0, 1, 2, 3
+
+
+def classify(m, zero_tol):
+    """identity / diagonal / monomial (one non-zero per row and column) / dense."""
+    nz = (np.abs(m.real) > zero_tol) | (np.abs(m.imag) > zero_tol)
+    off = nz & ~np.eye(m.shape[0], dtype=bool)
+    if not off.any():
+        return IDENTITY if np.all(np.abs(np.diag(m) - 1) <= zero_tol) else DIAGONAL
+    if np.all(nz.sum(axis=0) == 1) and np.all(nz.sum(axis=1) == 1):
+        return MONOMIAL
+    return DENSE
+
+
+def table_estimate(ms, k, cls):
+    """A measured gate time in integer nanoseconds (identity costs nothing;
+    a missing entry falls back to the dense entry, then to the largest)."""
+    if cls == IDENTITY:
+        return 0
+    v = ms[k][cls]
+    if not v > 0:
+        v = ms[k][DENSE]
+    if not v > 0:
+        v = max(ms[kk][c] for kk in range(1, len(ms)) for c in (1, 2, 3))
+    return int(round(v * 1e6))
+
+
 class Tile:
     def __init__(self, n):
         self.n = n
@@ -93,7 +120,7 @@ class Tile:
 
 
 class Fuser:
-    def __init__(self, n, mode, max_k, agglomerative, op_cap, zero_tol, amp_ops_per_pass):
+    def __init__(self, n, mode, max_k, agglomerative, op_cap, zero_tol, amp_ops_per_pass, cost=None):
         self.T = Tile(n)
         self.mode = mode
         self.max_k = max_k
@@ -101,6 +128,7 @@ class Fuser:
         self.op_cap = op_cap
         self.tol = zero_tol
         self.P = amp_ops_per_pass
+        self.cost = cost  # ms[k][class] table, or None for the operation-count model
 
     def info(self, block):
         if block.info is None:
@@ -110,6 +138,8 @@ class Fuser:
 
     def est(self, block):
         k = len(block.qubits)
+        if self.cost is not None:
+            return table_estimate(self.cost, k, classify(self.info(block)[0], self.tol))
         return max(self.P * 128, self.info(block)[1] << (7 - k))
 
     def fusible(self, top, bot, k):
@@ -186,9 +216,19 @@ class Fuser:
 
 
 def fuse(n, gates, theta=None, mode="adaptive", max_k=5, agglomerative=True, op_cap=4096,
-         zero_tol=1e-12, amp_ops_per_pass=82):
+         zero_tol=1e-12, amp_ops_per_pass=82, cost=None):
     """Fused gate list [(sorted qubits, matrix, operation count)] of a
-    workloads gate list."""
+    workloads gate list.  With a cost table (ms[k][class]) the adaptive test
+    compares measured times; with max_k = 0 every width 2..7 is tried and the
+    plan of least estimated total time kept (ties: the smaller width)."""
+    if cost is not None and max_k == 0:
+        best, best_plan = None, None
+        for k in range(2, 8):
+            plan = fuse(n, gates, theta, mode, k, agglomerative, op_cap, zero_tol, amp_ops_per_pass, cost)
+            total = sum(table_estimate(cost, len(q), classify(m, zero_tol)) for q, m, _ in plan)
+            if best is None or total < best:
+                best, best_plan = total, plan
+        return best_plan
     blocks = [Block(g.qubits, [(tuple(g.qubits), gate_matrix(g, theta))]) for g in gates]
     if mode == "none":  # every gate as given, re-expressed over its sorted qubits
         out = []
@@ -196,7 +236,7 @@ def fuse(n, gates, theta=None, mode="adaptive", max_k=5, agglomerative=True, op_
             m = block_matrix(b)
             out.append((b.qubits, m, opcount(m, zero_tol)))
         return out
-    F = Fuser(n, mode, max_k, agglomerative, op_cap, zero_tol, amp_ops_per_pass)
+    F = Fuser(n, mode, max_k, agglomerative, op_cap, zero_tol, amp_ops_per_pass, cost)
     for b in blocks:
         F.T.append(b)
     F.run()

@@ -41,10 +41,17 @@ class cast_circuit(ctypes.Structure):
                 ("gates", ctypes.POINTER(cast_gate)), ("n_params", ctypes.c_int32)]
 
 
+class cast_cost_table(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("ms", (ctypes.c_double * 4) * (CAST_MAX_K + 1)),
+                ("blocks_per_sm", (ctypes.c_int32 * 4) * (CAST_MAX_K + 1))]
+
+
 class cast_options(ctypes.Structure):
     _fields_ = [("fusion", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("agglomerative", ctypes.c_int32), ("op_cap", ctypes.c_int32),
-                ("zero_tol", ctypes.c_double), ("amp_ops_per_pass", ctypes.c_int32)]
+                ("zero_tol", ctypes.c_double), ("amp_ops_per_pass", ctypes.c_int32),
+                ("cost", ctypes.POINTER(cast_cost_table))]
 
 
 class cast_profile_entry(ctypes.Structure):
@@ -65,7 +72,7 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
            "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode",
            "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
-           "cast_set_f64_mode", "cast_get_f64_mode")
+           "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table")
 
 _lib = None
 
@@ -118,6 +125,8 @@ def load(build_if_missing=True):
         "cast_hea_destroy": (I, [P]),
         "cast_set_f64_mode": (I, [I]),
         "cast_get_f64_mode": (I, []),
+        "cast_autotune": (I, [I, I, P, P]),
+        "cast_set_cost_table": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -223,13 +232,40 @@ class _Circuit:
 
 
 def options(fusion="adaptive", max_k=5, agglomerative=True, op_cap=4096, zero_tol=1e-12,
-            amp_ops_per_pass=0):
+            amp_ops_per_pass=0, cost=None):
+    """cost: a cast_cost_table (from cast_autotune or cost_table()); the
+    options object keeps it alive."""
     o = cast_options()
     load().cast_options_default(ctypes.byref(o))
     o.fusion = {"none": 0, "size": 1, "adaptive": 2}[fusion] if isinstance(fusion, str) else fusion
     o.max_k, o.agglomerative, o.op_cap = max_k, int(bool(agglomerative)), op_cap
     o.zero_tol, o.amp_ops_per_pass = zero_tol, amp_ops_per_pass
+    if cost is not None:
+        o._cost_ref = cost
+        o.cost = ctypes.pointer(cost)
     return o
+
+
+def cost_table(ms, dtype="c64", n_qubits=0, blocks_per_sm=None):
+    """A cast_cost_table from nested lists ms[k][class] (k = 0..7; class 0
+    identity, 1 diagonal, 2 monomial, 3 dense)."""
+    t = cast_cost_table()
+    t.n_qubits, t.dtype = n_qubits, _dt(dtype)
+    for k in range(CAST_MAX_K + 1):
+        for c in range(4):
+            t.ms[k][c] = float(ms[k][c])
+            t.blocks_per_sm[k][c] = int(blocks_per_sm[k][c]) if blocks_per_sm is not None else 0
+    return t
+
+
+def cast_autotune(dtype, n_qubits, stream=0):
+    t = cast_cost_table()
+    _check(load().cast_autotune(_dt(dtype), int(n_qubits), ctypes.c_void_p(stream), ctypes.byref(t)))
+    return t
+
+
+def cast_set_cost_table(table):
+    _check(load().cast_set_cost_table(ctypes.byref(table) if table is not None else None))
 
 
 def _params_arr(params):

@@ -250,7 +250,7 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         DenseMat<R, K> U;
         for (int r = 0; r < (1 << K); r++)
             for (int c = 0; c < (1 << K); c++) U.m[r][c] = to_dev<R>(g.m[size_t(r) * (1 << K) + c]);
-        const int per_sm = K <= 3 ? 8 : (K == 4 ? 4 : 2);
+        const int per_sm = tuned_blocks_per_sm(sv->dt, K, CLS_DENSE, K <= 3 ? 8 : (K == 4 ? 4 : 2));
         ProfScope ps(sv->stream, "dense_k" + std::to_string(K) + "_" + dt_name(sv->dt),
                      2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
         k_dense<R, K><<<(unsigned)grid_for(ns, per_sm), 256, 0, sv->stream>>>(
@@ -292,7 +292,7 @@ cast_status run_diag(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
     const double frac = double(touched) / double(1 << K);
     ProfScope ps(sv->stream, "diag_k" + std::to_string(K) + "_" + dt_name(sv->dt),
                  2.0 * double(sizeof(T2)) * double(N) * frac, 6.0 * double(N) * frac);
-    k_diag<R, K><<<(unsigned)grid_for(N, 8), 256, 0, sv->stream>>>(
+    k_diag<R, K><<<(unsigned)grid_for(N, tuned_blocks_per_sm(sv->dt, K, CLS_DIAG, 8)), 256, 0, sv->stream>>>(
         reinterpret_cast<T2 *>(sv->data), N, tg, D);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
@@ -314,7 +314,7 @@ cast_status run_mono(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
     ProfScope ps(sv->stream, "mono_k" + std::to_string(K) + "_" + dt_name(sv->dt),
                  2.0 * double(sizeof(T2)) * double(ns << K) * frac,
                  g.unit_phases ? 0.0 : 6.0 * double(ns << K));
-    k_mono<R, K><<<(unsigned)grid_for(ns, 8), 256, 0, sv->stream>>>(
+    k_mono<R, K><<<(unsigned)grid_for(ns, tuned_blocks_per_sm(sv->dt, K, CLS_MONO, 8)), 256, 0, sv->stream>>>(
         reinterpret_cast<T2 *>(sv->data), ns, tg, M);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;

@@ -171,7 +171,8 @@ cast_status run_k(cast_sv *sv, const PreparedGate &g) {
             for (int c = 0; c < (1 << K); c++) U.m[r][c] = host_split(g.m[size_t(r) * (1 << K) + c]);
         ProfScope ps(sv->stream, "dfdense_k" + std::to_string(K) + "_c128", 32.0 * double(N),
                      8.0 * double(N << K));
-        k_dense_df<K><<<(unsigned)grid_for(ns, K <= 2 ? 8 : 4), 256, 0, sv->stream>>>(data, ns, tg, U);
+        k_dense_df<K><<<(unsigned)grid_for(ns, tuned_blocks_per_sm(CAST_C128, K, CLS_DENSE, K <= 2 ? 8 : 4)), 256, 0,
+                        sv->stream>>>(data, ns, tg, U);
     } else if (g.cls == CLS_DIAG) {
         DfDiag<K> Dg;
         Dg.skip = 0;
@@ -185,7 +186,8 @@ cast_status run_k(cast_sv *sv, const PreparedGate &g) {
         const double frac = double(touched) / double(1 << K);
         ProfScope ps(sv->stream, "dfdiag_k" + std::to_string(K) + "_c128", 32.0 * double(N) * frac,
                      6.0 * double(N) * frac);
-        k_diag_df<K><<<(unsigned)grid_for(N / 4, 8), 256, 0, sv->stream>>>(data, N, tg, Dg);
+        k_diag_df<K><<<(unsigned)grid_for(N / 4, tuned_blocks_per_sm(CAST_C128, K, CLS_DIAG, 8)), 256, 0,
+                       sv->stream>>>(data, N, tg, Dg);
     } else {
         DfMono<K> M;
         for (int j = 0; j < (1 << K); j++) {
@@ -193,7 +195,8 @@ cast_status run_k(cast_sv *sv, const PreparedGate &g) {
             M.perm[j] = (uint8_t)g.perm[j];
         }
         ProfScope ps(sv->stream, "dfmono_k" + std::to_string(K) + "_c128", 32.0 * double(N), 6.0 * double(N));
-        k_mono_df<K><<<(unsigned)grid_for(ns, 8), 256, 0, sv->stream>>>(data, ns, tg, M);
+        k_mono_df<K><<<(unsigned)grid_for(ns, tuned_blocks_per_sm(CAST_C128, K, CLS_MONO, 8)), 256, 0,
+                       sv->stream>>>(data, ns, tg, M);
     }
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;

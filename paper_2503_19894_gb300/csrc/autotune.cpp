@@ -1,0 +1,130 @@
+// Autotuner: measured per-gate costs (the GPU counterpart of the paper's
+// CostModel, Section IV-C) and the launch widths of the CUDA-core kernels.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace cast {
+
+namespace {
+std::mutex g_mu;
+cast_cost_table g_tab[2];
+bool g_have[2] = {false, false};
+
+// DFT matrix (dense, unitary), a phase diagonal, a cyclic shift with phases
+std::vector<cplx> sample_matrix(int k, int cls) {
+    const int d = 1 << k;
+    std::vector<cplx> m(size_t(d) * d, cplx(0.0, 0.0));
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) {
+            if (cls == CLS_DENSE) m[size_t(r) * d + c] = std::polar(1.0 / std::sqrt(double(d)), 2 * M_PI * r * c / d);
+            else if (cls == CLS_DIAG && r == c) m[size_t(r) * d + c] = std::polar(1.0, 0.7 + r);
+            else if (cls == CLS_MONO && c == (r + 1) % d) m[size_t(r) * d + c] = std::polar(1.0, 0.3 + r);
+        }
+    return m;
+}
+}  // namespace
+
+int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int i = dt == CAST_C64 ? 0 : 1;
+    if (!g_have[i] || k < 1 || k > CAST_MAX_K || cls < 0 || cls > 3) return def;
+    const int v = g_tab[i].blocks_per_sm[k][cls];
+    return v > 0 ? v : def;
+}
+
+// cost-table estimate of a block (integer nanoseconds), used by the fusion pass
+int64_t table_estimate(const cast_cost_table &t, int k, int cls) {
+    double ms = t.ms[k][cls];
+    if (cls != CLS_IDENTITY && !(ms > 0)) ms = t.ms[k][CLS_DENSE];
+    if (cls != CLS_IDENTITY && !(ms > 0)) {
+        for (int kk = 1; kk <= CAST_MAX_K; kk++)
+            for (int c = 1; c < 4; c++) ms = std::max(ms, t.ms[kk][c]);
+    }
+    return cls == CLS_IDENTITY ? 0 : int64_t(std::llround(ms * 1e6));
+}
+
+}  // namespace cast
+
+using namespace cast;
+
+extern "C" {
+
+cast_status cast_set_cost_table(const cast_cost_table *t) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!t) {
+        g_have[0] = g_have[1] = false;
+        return CAST_OK;
+    }
+    if (t->dtype != CAST_C64 && t->dtype != CAST_C128) return fail(CAST_ERR_ARG, "cost table has an unknown dtype");
+    const int i = t->dtype == CAST_C64 ? 0 : 1;
+    g_tab[i] = *t;
+    g_have[i] = true;
+    return CAST_OK;
+}
+
+cast_status cast_autotune(cast_dtype dt, int n, void *stream, cast_cost_table *out) {
+    if (!out) return fail(CAST_ERR_ARG, "null output table");
+    if (dt != CAST_C64 && dt != CAST_C128) return fail(CAST_ERR_ARG, "unknown dtype");
+    if (n < CAST_MAX_K + 1 || n > 30) return fail(CAST_ERR_ARG, "autotune state size must be in 8..30 qubits");
+    cast_sv *sv = nullptr;
+    cast_status st = cast_sv_create(n, dt, stream, &sv);
+    if (st != CAST_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->n_qubits = n;
+    out->dtype = dt;
+    const int ti = dt == CAST_C64 ? 0 : 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int widths[4] = {1, 2, 4, 8};
+    for (int k = 1; k <= CAST_MAX_K && st == CAST_OK; k++) {
+        int qs[CAST_MAX_K];
+        for (int i = 0; i < k; i++) qs[i] = k == 1 ? n / 2 : int(std::lround(double(i) * (n - 1) / (k - 1)));
+        for (int cls = CLS_DIAG; cls <= CLS_DENSE && st == CAST_OK; cls++) {
+            std::vector<cplx> m = sample_matrix(k, cls);
+            PreparedGate g;
+            if ((st = prepare_gate(n, qs, k, m.data(), 1e-12, &g)) != CAST_OK) break;
+            double best = 0;
+            int best_w = 0;
+            for (int wi = 0; wi < 4 && st == CAST_OK; wi++) {
+                {  // try this width through the process-wide table
+                    std::lock_guard<std::mutex> lk(g_mu);
+                    cast_cost_table t = g_have[ti] ? g_tab[ti] : *out;
+                    t.dtype = dt;
+                    t.blocks_per_sm[k][cls] = widths[wi];
+                    g_tab[ti] = t;
+                    g_have[ti] = true;
+                }
+                for (int rep = 0; rep < 2 && st == CAST_OK; rep++) st = launch_gate(sv, g);  // warm-up
+                if (st != CAST_OK) break;
+                cudaEventRecord(e0, sv->stream);
+                const int reps = 3;
+                for (int rep = 0; rep < reps && st == CAST_OK; rep++) st = launch_gate(sv, g);
+                cudaEventRecord(e1, sv->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune timing");
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = double(ms) / reps;
+                if (best_w == 0 || per < best) {
+                    best = per;
+                    best_w = widths[wi];
+                }
+            }
+            out->ms[k][cls] = best;
+            out->blocks_per_sm[k][cls] = best_w;
+        }
+    }
+    {  // leave the process-wide table as it was before the call
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_have[ti] = false;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cast_status st2 = cast_sv_destroy(sv);
+    return st != CAST_OK ? st : st2;
+}
+
+}  // extern "C"

@@ -214,6 +214,7 @@ void cast_options_default(cast_options *o) {
     o->op_cap = 4096;
     o->zero_tol = 1e-12;
     o->amp_ops_per_pass = 0;
+    o->cost = nullptr;
 }
 
 int64_t cast_opcount(const double *matrix, int k, double zero_tol) {
@@ -328,7 +329,8 @@ static cast_options resolve_options(const cast_options *opt, cast_dtype dt) {
 
 static cast_status check_options(const cast_options &o) {
     if (o.fusion < CAST_FUSE_NONE || o.fusion > CAST_FUSE_ADAPTIVE) return fail(CAST_ERR_ARG, "unknown fusion mode");
-    if (o.max_k < 1 || o.max_k > CAST_MAX_K) return fail(CAST_ERR_ARG, "max_k must be in 1..7");
+    if (o.max_k < (o.cost ? 0 : 1) || o.max_k > CAST_MAX_K)
+        return fail(CAST_ERR_ARG, "max_k must be in 1..7 (0 = chosen from a cost table)");
     if (!(o.zero_tol >= 0.0) || !std::isfinite(o.zero_tol)) return fail(CAST_ERR_ARG, "bad zero_tol");
     return CAST_OK;
 }

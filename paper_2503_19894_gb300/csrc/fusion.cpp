@@ -111,6 +111,7 @@ struct Fuser {
 
     int64_t cost(const Block &b) const {
         const int k = (int)b.q.size();
+        if (opt.cost) return table_estimate(*opt.cost, k, classify_matrix(b.m.data(), k, opt.zero_tol));
         const int64_t mem = P * 128;
         const int64_t cmp = b.ops << (7 - k);
         return mem > cmp ? mem : cmp;
@@ -240,8 +241,33 @@ int64_t default_amp_ops_per_pass(cast_dtype dt) {
     return f64_mode() == CAST_F64_EMULATED ? 16 : 2;
 }
 
+static cast_status fuse_once(const cast_circuit *c, const double *params, const cast_options *opt,
+                             std::vector<FusedGate> *out);
+
+// With a cost table and max_k = 0, try every fusion width and keep the plan of
+// least estimated time (ties: the smaller width).
 cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast_options *opt,
                          std::vector<FusedGate> *out) {
+    if (!(opt->cost && opt->max_k == 0)) return fuse_once(c, params, opt, out);
+    int64_t best = -1;
+    for (int k = 2; k <= CAST_MAX_K; k++) {
+        cast_options o = *opt;
+        o.max_k = k;
+        std::vector<FusedGate> cand;
+        cast_status st = fuse_once(c, params, &o, &cand);
+        if (st != CAST_OK) return st;
+        int64_t total = 0;
+        for (const FusedGate &g : cand) total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol));
+        if (best < 0 || total < best) {
+            best = total;
+            out->swap(cand);
+        }
+    }
+    return CAST_OK;
+}
+
+static cast_status fuse_once(const cast_circuit *c, const double *params, const cast_options *opt,
+                             std::vector<FusedGate> *out) {
     Fuser F{*opt, opt->amp_ops_per_pass > 0 ? opt->amp_ops_per_pass : default_amp_ops_per_pass(CAST_C64), {}, {}, {c->n_qubits, {}}};
     for (int g = 0; g < c->n_gates; g++) {
         const cast_gate &gt = c->gates[g];

@@ -113,6 +113,32 @@ cast_status gate_matrix_of(const cast_gate &g, const double *params, int n_param
     return gate_table_matrix(g.kind, g.k, p, out);
 }
 
+int classify_matrix(const cplx *m, int k, double tol) {
+    const int d = 1 << k;
+    auto nz = [&](int r, int c) {
+        const cplx v = m[size_t(r) * d + c];
+        return std::fabs(v.real()) > tol || std::fabs(v.imag()) > tol;
+    };
+    bool diag = true, ident = true;
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) {
+            if (r != c && nz(r, c)) diag = false;
+            if (r == c && std::abs(m[size_t(r) * d + c] - cplx(1.0, 0.0)) > tol) ident = false;
+        }
+    if (diag) return ident ? CLS_IDENTITY : CLS_DIAG;
+    for (int r = 0; r < d; r++) {
+        int cnt = 0;
+        for (int c = 0; c < d; c++) cnt += nz(r, c);
+        if (cnt != 1) return CLS_DENSE;
+    }
+    for (int c = 0; c < d; c++) {
+        int cnt = 0;
+        for (int r = 0; r < d; r++) cnt += nz(r, c);
+        if (cnt != 1) return CLS_DENSE;
+    }
+    return CLS_MONO;
+}
+
 int64_t opcount(const cplx *m, int k, double tol) {
     const size_t n = size_t(1) << (2 * k);
     int64_t nz = 0;

@@ -140,6 +140,13 @@ cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
+// Autotuned launch width (blocks per SM) of a CUDA-core kernel, or def.
+int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def);
+// Cost-table estimate of one gate of size k and class cls, in integer ns.
+int64_t table_estimate(const cast_cost_table &t, int k, int cls);
+// Class of a 2^k x 2^k matrix (identity / diagonal / monomial / dense).
+int classify_matrix(const cplx *m, int k, double zero_tol);
+
 // Double-float path for complex128 gates (apply_df.cu).
 bool df_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_df(cast_sv *sv, const PreparedGate &g);

@@ -73,3 +73,28 @@ def test_benchmark_plans_match_oracle(which, P):
     gates = W.qft_circuit(n) if which == "qft30" else W.random_circuit(n, 30, 1)
     ref = _compare(n, gates, None, fusion="adaptive", max_k=5, agglomerative=True, amp_ops_per_pass=P)
     assert len(ref) < len(gates) / 3
+
+
+# a measured-looking cost table (ms per gate at 26 qubits, complex64):
+# memory-bound up to k = 4, growing beyond, sparse classes cheaper
+SAMPLE_MS = [[0, 0, 0, 0],
+             [0, 0.15, 0.16, 0.17], [0, 0.15, 0.16, 0.17], [0, 0.16, 0.17, 0.18],
+             [0, 0.16, 0.18, 0.19], [0, 0.17, 0.19, 0.21], [0, 0.18, 0.22, 0.45], [0, 0.2, 0.3, 1.6]]
+
+
+@pytest.mark.parametrize("name,n,make", CASES)
+@pytest.mark.parametrize("max_k", [3, 5, 0])
+def test_cost_table_fusion_matches_oracle(name, n, make, max_k):
+    gates = make()
+    theta = W.uniform_params(2 * n * 3, -3, 3, 0) if name.startswith("hea") else None
+    table = capi.cost_table(SAMPLE_MS)
+    got = capi.cast_fuse(n, gates, theta, opts=capi.options("adaptive", max_k, cost=table))
+    ref = ofu.fuse(n, gates, theta, mode="adaptive", max_k=max_k, cost=SAMPLE_MS)
+    assert [q for q, _, _ in got] == [q for q, _, _ in ref]
+    for (_, a, _), (_, b, _) in zip(got, ref):
+        assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_max_k_zero_needs_a_cost_table():
+    with pytest.raises(capi.CastError):
+        capi.cast_fuse(4, W.random_circuit(4, 2, 0), opts=capi.options("adaptive", 0))
