@@ -13,22 +13,25 @@
 //   group g >= 1 qubits T+(g-1)G .. T+gG-1  (G = T-5), tile = those qubits
 //                plus index bits 0..4 (runs of 32 amplitudes stay coalesced)
 // A layer is then ~n/G passes.  Rotations on different qubits commute, so the
-// order "RY on all, RZ on all" equals "RZ_q RY_q" qubit by qubit; the CZ ladder
-// is diagonal and is applied, as a sign from the global index, when the last
-// group's tile is stored.  Inside a tile the rotations run in rounds of up to
-// three qubits: each thread gathers the 8 amplitudes of a sub-slice from
-// shared memory, applies the three 2x2 gates in registers and scatters them
-// back, so shared memory is crossed once per three qubits.
+// layer "RY on all, RZ on all, CZ ladder" is applied per group as: the RY
+// gates in register rounds of up to three qubits (each thread gathers the 8
+// amplitudes of a sub-slice, applies three 2x2 rotations, scatters them back),
+// then the group's RZ gates together as one diagonal phase looked up from two
+// small tables, then (last group) the CZ ladder as a sign from the global
+// index, both while the tile is stored.  The tile is XOR-swizzled in shared
+// memory so that sub-slices of low qubits do not collide in the banks.
 //
 // Energies: one read-only pass per group; group 0 also forms the diagonal
 // ZZ part; the X_q terms of a group's qubits are formed from amplitude pairs
 // inside the tile.  lambda = H psi is built the same way (group 0 writes, the
 // others accumulate).  The adjoint backward sweep visits the layers in reverse
 // and, per layer, the groups in reverse (the last group first, undoing the CZ
-// ladder at load); for each qubit it forms Im<lam|Z|psi> then un-applies RZ,
-// then Im<lam|Y|psi> and un-applies RY, on psi and lam together.  Because the
-// gradient of a gate is unchanged by reordering gates that commute with it,
-// processing qubit by qubit gives the gradients of the layer-ordered circuit.
+// ladder at load); it forms every Im<lam|Z_q|psi> of the group from one sweep
+// (the RZ gates commute with each other and act last) and un-applies their
+// diagonal, then per qubit forms Im<lam|Y_q|psi> and un-applies RY, on psi and
+// lam together.  Because the gradient of a gate is unchanged by reordering
+// gates that commute with it, this gives the gradients of the layer-ordered
+// circuit.
 //
 // Work distribution: one launch per (layer, group) covers the tiles of every
 // instance that has that group; each CTA takes a contiguous range of the tile
@@ -131,6 +134,48 @@ __device__ __forceinline__ bool cz_ladder_odd(uint64_t x, int n) {
     return __popcll(x & (x >> 1) & m) & 1;
 }
 
+// XOR swizzle of the shared tile: bits 0..2 of the slot are flipped by bits
+// 3..5 of the index, so gathering 8 amplitudes that differ in index bits 0..2
+// (stride 8 across threads) spreads over the banks.  Bijective on any tile.
+__device__ __forceinline__ uint32_t sw(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+
+// Phase of the group's RZ gates for local index l: product over the rotated
+// qubits of (cz - i sz) (bit 0) or (cz + i sz) (bit 1), looked up from two
+// tables of up to 64 entries (rotated bits 0..5 and 6..11 of the group).
+template <typename R>
+__device__ void build_phase_tables(typename Cx<R>::T *ph0, typename Cx<R>::T *ph1, const Geo &G,
+                                   const Rot<R> *rots) {
+    using T2 = typename Cx<R>::T;
+    const int n0 = G.nrot < 6 ? G.nrot : 6, n1 = G.nrot - n0;
+    for (int e = threadIdx.x; e < (1 << n0) + (1 << n1); e += blockDim.x) {
+        const bool first = e < (1 << n0);
+        const int idx = first ? e : e - (1 << n0);
+        const int nb = first ? n0 : n1, r0 = first ? 0 : 6;
+        R re = 1, im = 0;
+        for (int i = 0; i < nb; i++) {
+            const Rot<R> r = rots[G.q0 + r0 + i];
+            const R s = ((idx >> i) & 1) ? r.sz : -r.sz;  // cz + i s
+            const R nre = re * r.cz - im * s, nim = re * s + im * r.cz;
+            re = nre;
+            im = nim;
+        }
+        T2 v;
+        v.x = re;
+        v.y = im;
+        if (first) ph0[idx] = v;
+        else ph1[idx] = v;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T group_phase(const typename Cx<R>::T *ph0,
+                                                         const typename Cx<R>::T *ph1, const Geo &G, uint32_t l) {
+    const int n0 = G.nrot < 6 ? G.nrot : 6, n1 = G.nrot - n0;
+    const typename Cx<R>::T a = ph0[(l >> G.rb0) & ((1u << n0) - 1)];
+    if (n1 == 0) return a;
+    return cmul(a, ph1[(l >> (G.rb0 + 6)) & ((1u << n1) - 1)]);
+}
+
 // locate the instance of global tile index gt (binary search on the prefix)
 __device__ __forceinline__ int find_inst(const PassArgs &P, uint64_t gt) {
     int lo = 0, hi = P.ninst - 1;
@@ -153,26 +198,11 @@ __device__ __forceinline__ void ry(double2 &a, double2 &b, double c, double s) {
     a.x = c * x.x - s * y.x; a.y = c * x.y - s * y.y;
     b.x = s * x.x + c * y.x; b.y = s * x.y + c * y.y;
 }
-// multiply by (cz - i sz) (bit 0) or (cz + i sz) (bit 1); sgn = -1 / +1
-template <typename T2, typename R>
-__device__ __forceinline__ void rz1(T2 &a, R cz, R sz) {
-    const T2 x = a;
-    a.x = cz * x.x + sz * x.y;
-    a.y = cz * x.y - sz * x.x;
-}
-template <typename T2, typename R>
-__device__ __forceinline__ void rz2(T2 &b, R cz, R sz) {
-    const T2 x = b;
-    b.x = cz * x.x - sz * x.y;
-    b.y = cz * x.y + sz * x.x;
-}
-
-// forward: RZ_q RY_q on the pair (a, b) of qubit q
+// forward: RY_q on the pair (a, b) of qubit q (the group's RZ gates follow as
+// one diagonal phase when the tile is stored)
 template <typename T2, typename R>
 __device__ __forceinline__ void fwd_pair(T2 &a, T2 &b, const Rot<R> &r) {
     ry(a, b, r.cy, r.sy);
-    rz1(a, r.cz, r.sz);
-    rz2(b, r.cz, r.sz);
 }
 
 // apply the forward rotations of local bits bits[0..nb) (nb <= 3) to the tile
@@ -194,7 +224,7 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            v[j] = tile[o];
+            v[j] = tile[sw(o)];
         }
 #pragma unroll
         for (int i = 0; i < NB; i++)
@@ -207,7 +237,7 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            tile[o] = v[j];
+            tile[sw(o)] = v[j];
         }
     }
 }
@@ -253,7 +283,7 @@ __device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename Cx<R>::T
 #pragma unroll
     for (int i = 0; i < TileRegs<R>::IT; i++) {
         const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
-        if (l < sz) tile[l] = b.v[i];
+        if (l < sz) tile[sw(l)] = b.v[i];
     }
 }
 
@@ -264,11 +294,13 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
     using T2 = typename Cx<R>::T;
     constexpr int T = tile_bits<R>();
     __shared__ __align__(16) T2 tile[1 << T];
+    __shared__ __align__(16) T2 ph0[64], ph1[64];
     const uint64_t total = P.prefix[P.ninst];
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
     if (t_begin >= t_end) return;
+    int table_inst = -1;
     // the next tile's loads are issued before this tile's rotations run
     TileRegs<R> buf;
     int k = find_inst(P, t_begin);
@@ -290,12 +322,21 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
             t = gt + 1 - P.prefix[k];
             tile_load<R>(buf, arena + I.off, G, t);
         }
-        apply_rotations<R>(tile, Gc, rot + Ic.rot_off + size_t(P.layer) * Ic.n);
+        const Rot<R> *lr = rot + Ic.rot_off + size_t(P.layer) * Ic.n;
+        // the phase tables depend on the instance only (the tile list of an
+        // instance starts at prefix = gt - tc); rebuilt when it changes and
+        // published by the barrier after the first rotation round
+        const int inst_id = int(gt - tc);
+        if (inst_id != table_inst) {
+            build_phase_tables<R>(ph0, ph1, Gc, lr);
+            table_inst = inst_id;
+        }
+        apply_rotations<R>(tile, Gc, lr);
         const bool last = P.group == Ic.ngroups - 1;
         T2 *sv = arena + Ic.off;
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
             const uint64_t x = tile_global(Gc, tc, l);
-            T2 v = tile[l];
+            T2 v = cmul(group_phase<R>(ph0, ph1, Gc, l), tile[sw(l)]);
             if (last && cz_ladder_odd(x, Ic.n)) {
                 v.x = -v.x;
                 v.y = -v.y;
@@ -372,7 +413,7 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
             const int b = G.rb0 + r;
             for (uint32_t p = threadIdx.x; p < (sz >> 1); p += blockDim.x) {
                 const uint32_t l0 = ((p >> b) << (b + 1)) | (p & ((1u << b) - 1));
-                const T2 a = tile[l0], c = tile[l0 | (1u << b)];
+                const T2 a = tile[sw(l0)], c = tile[sw(l0 | (1u << b))];
                 acc.add(R(2.0 * hx) * (a.x * c.x + a.y * c.y));
             }
         }
@@ -417,13 +458,13 @@ k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__res
             if (P.group == 0) {
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
                 const R d = R(zz * double(I.n - 1 - 2 * odd));
-                out.x = d * tile[l].x;
-                out.y = d * tile[l].y;
+                out.x = d * tile[sw(l)].x;
+                out.y = d * tile[sw(l)].y;
             } else {
                 out = lam[I.off + x];
             }
             for (int r = 0; r < G.nrot; r++) {
-                const T2 nb = tile[l ^ (1u << (G.rb0 + r))];
+                const T2 nb = tile[sw(l ^ (1u << (G.rb0 + r)))];
                 out.x += R(hx) * nb.x;
                 out.y += R(hx) * nb.y;
             }
@@ -433,10 +474,11 @@ k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__res
     }
 }
 
-// backward sweep of one (layer, group) on psi and lam, with gradients
+// backward sweep of one (layer, group) on psi and lam, with gradients: the RY
+// part of a round (the RZ gates were handled as one diagonal beforehand)
 template <typename R, int NB>
 __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, const int *bits, const Rot<R> *rot,
-                          Acc<R> (&gz)[3], Acc<R> (&gy)[3]) {
+                          Acc<R> (&gy)[3]) {
     using T2 = typename Cx<R>::T;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
@@ -453,22 +495,17 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            p[j] = tp[o];
-            l[j] = tl[o];
+            p[j] = tp[sw(o)];
+            l[j] = tl[sw(o)];
         }
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             const Rot<R> r = rot[i];
-            R sz = 0, sy = 0;  // this sub-slice's share, added to the compensated sums once
+            R sy = 0;  // this sub-slice's share, added to the compensated sum once
 #pragma unroll
             for (int j = 0; j < (1 << NB); j++) {
                 if ((j >> i) & 1) continue;
                 T2 &p0 = p[j], &p1 = p[j | (1 << i)], &l0 = l[j], &l1 = l[j | (1 << i)];
-                // dE/dphi = Im<lam|Z|psi> = Im(conj(l0) p0) - Im(conj(l1) p1)
-                sz += (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
-                // un-apply RZ: multiply by (cz + i sz) on bit 0, (cz - i sz) on bit 1
-                rz2(p0, r.cz, r.sz); rz1(p1, r.cz, r.sz);
-                rz2(l0, r.cz, r.sz); rz1(l1, r.cz, r.sz);
                 // dE/dtheta = Im<lam|Y|psi>; Y psi = (-i p1, i p0)
                 //   Im(conj(l0)(-i p1)) = -(l0.x p1.x + l0.y p1.y); Im(conj(l1)(i p0)) = l1.x p0.x + l1.y p0.y
                 sy += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
@@ -476,7 +513,6 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
                 ry(p0, p1, r.cy, -r.sy);
                 ry(l0, l1, r.cy, -r.sy);
             }
-            gz[i].add(sz);
             gy[i].add(sy);
         }
 #pragma unroll
@@ -485,8 +521,8 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            tp[o] = p[j];
-            tl[o] = l[j];
+            tp[sw(o)] = p[j];
+            tl[sw(o)] = l[j];
         }
     }
 }
@@ -502,6 +538,8 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
     T2 *tp = reinterpret_cast<T2 *>(hea_smem);
     T2 *tl = tp + (1 << T);
     __shared__ double gacc[2 * T];  // [RY of each rotated qubit][RZ of each]
+    __shared__ __align__(16) T2 ph0[64], ph1[64];
+    int table_inst = -1;
     const uint64_t total = P.prefix[P.ninst];
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
@@ -553,11 +591,42 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                     a.x = -a.x;
                     a.y = -a.y;
                 }
-                dst[l] = a;
+                dst[sw(l)] = a;
+            }
+        }
+        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
+        if (int(gt - t) != table_inst) {  // new instance: its RZ phase tables
+            build_phase_tables<R>(ph0, ph1, G, lr);
+            table_inst = int(gt - t);
+        }
+        __syncthreads();
+        // the group's RZ gates act last in the layer and commute: every
+        // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x) is taken
+        // from the same state, then the diagonal is un-applied from psi and lam
+        {
+            R gzr[T];
+#pragma unroll
+            for (int r = 0; r < T; r++) gzr[r] = 0;
+            for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
+                const uint32_t o = sw(l);
+                T2 a = tp[o], b = tl[o];
+                const R w = b.x * a.y - b.y * a.x;
+#pragma unroll
+                for (int r = 0; r < T; r++)
+                    if (r < G.nrot) gzr[r] += ((l >> (G.rb0 + r)) & 1) ? -w : w;
+                T2 ph = group_phase<R>(ph0, ph1, G, l);
+                ph.y = -ph.y;  // conjugate
+                tp[o] = cmul(ph, a);
+                tl[o] = cmul(ph, b);
+            }
+#pragma unroll
+            for (int r = 0; r < T; r++) {
+                if (r >= G.nrot) continue;
+                const double v = warp_sum(double(gzr[r]));
+                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[T + r], v);
             }
         }
         __syncthreads();
-        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
         for (int r0 = 0; r0 < G.nrot; r0 += 3) {
             const int nb = G.nrot - r0 < 3 ? G.nrot - r0 : 3;
             int bits[3];
@@ -566,23 +635,20 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                 bits[i] = G.rb0 + r0 + i;
                 rr[i] = lr[G.q0 + r0 + i];
             }
-            Acc<R> gz[3], gy[3];
-            if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gz, gy);
-            else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gz, gy);
-            else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gz, gy);
+            Acc<R> gy[3];
+            if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
+            else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
+            else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
             for (int i = 0; i < nb; i++) {
-                const double vz = warp_sum(gz[i].value()), vy = warp_sum(gy[i].value());
-                if ((threadIdx.x & 31) == 0) {
-                    atomicAdd(&gacc[T + r0 + i], vz);
-                    atomicAdd(&gacc[r0 + i], vy);
-                }
+                const double vy = warp_sum(gy[i].value());
+                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[r0 + i], vy);
             }
             __syncthreads();
         }
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
             const uint64_t x = tile_global(G, t, l);
-            psi[I.off + x] = tp[l];
-            lam[I.off + x] = tl[l];
+            psi[I.off + x] = tp[sw(l)];
+            lam[I.off + x] = tl[sw(l)];
         }
         __syncthreads();
     }
