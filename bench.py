@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-vqa", action="store_true")
+    p.add_argument("--no-c128", action="store_true")
     return p.parse_args()
 
 
@@ -209,6 +210,51 @@ def _time(fn, reps):
         fn()
     torch.cuda.synchronize()
     return (time.perf_counter() - t0) / reps
+
+
+def secondary_dtype(n, layers, max_k, dtype, steps=1, warmup=1):
+    """The same step on the other state type (device-resident; no e2e)."""
+    import torch
+
+    import paper_2503_19894_gb300 as pkg
+    from paper_2503_19894_gb300 import capi
+    S = 8 if dtype == "c64" else 16
+    x, qft, rqc = workload(n, layers)
+    opts = capi.options("adaptive", max_k)
+    pq = capi.cast_plan_create(n, qft, opts=opts, dtype=dtype)
+    pr = capi.cast_plan_create(n, rqc, opts=opts, dtype=dtype)
+    gates = capi.cast_plan_info(pq)[0] + capi.cast_plan_info(pr)[0]
+    sv = pkg.StateVector(n, dtype, init_index=x)
+    z0 = W.z0_observable()
+
+    def step():
+        capi.cast_sv_set_basis(sv.handle, x)
+        capi.cast_plan_apply(sv.handle, pq)
+        capi.cast_plan_apply(sv.handle, pr)
+        return capi.cast_expectation(sv.handle, z0)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capi.cast_profile_begin()
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = capi.cast_profile_end()
+    ms = e0.elapsed_time(e1) / steps
+    sv.close()
+    capi.cast_plan_destroy(pq)
+    capi.cast_plan_destroy(pr)
+    top = prof[0]
+    return {"state": "complex128" if S == 16 else "complex64",
+            "arithmetic": "double-float on FP32" if (S == 16 and capi.cast_get_f64_mode() == 0) else "native",
+            "value": round(gates * 2.0 * (1 << n) * S / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms, 1), "fused_gates": gates, "steps": steps, "warmup": warmup,
+            "top_kernel": {"name": top["name"], "launches": top["launches"],
+                           "avg_ms": round(top["ms"] / top["launches"], 3),
+                           "gflops": round(top["flops"] / (top["ms"] / 1e3) / 1e9, 1)}}
 
 
 def vqa_bench():
@@ -429,6 +475,8 @@ def main():
                 "clocks": clk.summary(),
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in p.items()}
                             for p in prof[:8]]}
+        if world == 1 and not a.no_c128:
+            line["other_dtype"] = secondary_dtype(n, a.layers, a.max_k, "c128" if S == 8 else "c64")
         if world == 1 and not a.no_vqa:
             line["vqa"] = vqa_bench()
         if world == 1 and not a.no_cpu:

@@ -110,6 +110,15 @@ cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double 
 cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 
+/* Failure-detection test hook.  The next tensor-core gate launch waits on an
+ * MMA completion that never comes (its issuing thread skips the MMAs), with
+ * the barrier wait bounded to wait_limit polls instead of the default 2^26:
+ * every CTA gives up, frees its tensor memory and returns; the error is
+ * reported as CAST_ERR_TIMEOUT by the next call that synchronises with the
+ * state (copy_to_host, expectation, adjoint_grad).  The state's contents are
+ * then unspecified; the CUDA context stays usable.  Nothing traps or hangs. */
+cast_status cast_debug_inject_timeout(uint32_t wait_limit);
+
 /* Arithmetic for complex128 gates (process-wide setting):
  *   CAST_F64_EMULATED (default): dense (k <= 5), diagonal and phased
  *     monomial gates in double-float arithmetic on the FP32 pipe (pairs of

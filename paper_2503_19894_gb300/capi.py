@@ -72,7 +72,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_plan_destroy", "cast_profile_begin", "cast_profile_end",
            "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode",
            "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
-           "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table")
+           "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table",
+           "cast_debug_inject_timeout")
 
 _lib = None
 
@@ -127,6 +128,7 @@ def load(build_if_missing=True):
         "cast_get_f64_mode": (I, []),
         "cast_autotune": (I, [I, I, P, P]),
         "cast_set_cost_table": (I, [P]),
+        "cast_debug_inject_timeout": (I, [ctypes.c_uint32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -462,6 +464,10 @@ def cast_hea_grad(b, params, zz, hx, n_instances):
 
 def cast_hea_destroy(b):
     _check(load().cast_hea_destroy(ctypes.c_void_p(b)))
+
+
+def cast_debug_inject_timeout(wait_limit):
+    _check(load().cast_debug_inject_timeout(int(wait_limit)))
 
 
 def cast_last_error():

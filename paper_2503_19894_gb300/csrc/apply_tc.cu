@@ -56,7 +56,10 @@ namespace {
 __device__ int g_tc_error;
 std::atomic<int> g_tensor_mode{CAST_TC_TF32X3};
 
-constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kWaitLimit = 1u << 26;  // polls of the MMA barrier (~1 s)
+// test hook (cast_debug_inject_timeout): the issuing thread skips its MMAs
+// and commit, so every wait of the next launch runs out
+std::atomic<uint32_t> g_inject_limit{0};
 
 // The hi/lo split of U: by value in the launch parameters for k <= 5 (at most
 // 16 KB), through a device buffer for k = 6 (64 KB, beyond the 32 KB limit).
@@ -90,7 +93,7 @@ struct TcShape {
 template <int K>
 __global__ void __launch_bounds__(TcShape<K>::NT, TcShape<K>::CTAS_PER_SM)
 k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-           const __grid_constant__ TcMat<K> U) {
+           const __grid_constant__ TcMat<K> U, uint32_t wait_limit, int skip_mma) {
     using S = TcShape<K>;
     constexpr int NK = S::NK, MPT = S::MPT;
     constexpr uint32_t IDESC = tc::idesc_tf32(128, NK);
@@ -185,7 +188,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        if (tid == 0) {
+        if (tid == 0 && !skip_mma) {
             const uint32_t wH = tc::smem_u32(sWhi), wL = tc::smem_u32(sWlo);
             uint32_t acc = 0;
 #pragma unroll
@@ -201,7 +204,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
             }
             tc::mma_commit(mbar);
         }
-        const bool ok = tc::mbar_wait(mbar, phase, kWaitLimit);
+        const bool ok = tc::mbar_wait(mbar, phase, wait_limit);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -246,7 +249,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     }
     if (failed) {
         if (tid == 0) atomicOr(&g_tc_error, 1);
-        tc::mbar_wait(mbar, phase, kWaitLimit);  // let an MMA in flight finish before freeing TMEM
+        tc::mbar_wait(mbar, phase, wait_limit);  // let an MMA in flight finish before freeing TMEM
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -305,7 +308,9 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     const uint64_t grid = ntiles < cap ? ntiles : cap;
     ProfScope ps(sv->stream, "tc_k" + std::to_string(K) + "_c64", 16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
-    k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U);
+    const uint32_t inject = g_inject_limit.exchange(0);
+    k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U,
+                                                               inject ? inject : kWaitLimit, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
 }
@@ -346,5 +351,11 @@ cast_status cast_set_tensor_mode(int mode) {
 }
 
 int cast_get_tensor_mode(void) { return cast::g_tensor_mode.load(); }
+
+cast_status cast_debug_inject_timeout(uint32_t wait_limit) {
+    if (wait_limit == 0) return cast::fail(CAST_ERR_ARG, "wait limit must be positive");
+    cast::g_inject_limit = wait_limit;
+    return CAST_OK;
+}
 
 }  // extern "C"

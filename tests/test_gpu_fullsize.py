@@ -108,3 +108,25 @@ def test_rqc30_fused_then_inverse_returns(dtype, layers):
     sv.close()
     capi.cast_plan_destroy(pf)
     capi.cast_plan_destroy(pi)
+
+
+@pytest.mark.parametrize("n,dtype,k", [(33, "c64", 5), (32, "c128", 3)])
+def test_largest_states(n, dtype, k):
+    """64 GiB states (2^33 complex64 / 2^32 complex128 amplitudes): slice
+    counts above 2^31 and byte offsets above 2^35; a dense gate on a basis
+    state reproduces the matrix column, and its inverse restores |x>."""
+    rng = np.random.default_rng(n)
+    qs = (0, n // 2, n - 1) + tuple(range(3, 3 + k - 3))
+    u = W.haar_unitary(k, rng)
+    x = (1 << (n - 1)) | (1 << (n // 2)) | 5
+    sv = pkg.StateVector(n, dtype, init_index=x)
+    sv.apply_gate(qs, u)
+    jx = sum(((x >> q) & 1) << i for i, q in enumerate(qs))
+    base = x & ~sum(1 << q for q in qs)
+    idx = np.array([base | sum(((j >> i) & 1) << q for i, q in enumerate(qs)) for j in range(1 << k)])
+    assert np.max(np.abs(sampled(sv, idx) - u[:, jx])) <= TOL[dtype]
+    sv.apply_gate(qs, u.conj().T)
+    assert abs(sampled(sv, np.array([x]))[0] - 1.0) <= 10 * TOL[dtype]
+    assert abs(sv.expectation(IDENTITY) - 1.0) <= 10 * TOL[dtype]
+    sv.close()
+    torch.cuda.empty_cache()
