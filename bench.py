@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-vqa", action="store_true")
     p.add_argument("--no-c128", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="add the dense-gate sweep (k = 1..7, low/high/mixed targets, every arithmetic mode)")
     return p.parse_args()
 
 
@@ -255,6 +257,57 @@ def secondary_dtype(n, layers, max_k, dtype, steps=1, warmup=1):
             "top_kernel": {"name": top["name"], "launches": top["launches"],
                            "avg_ms": round(top["ms"] / top["launches"], 3),
                            "gflops": round(top["flops"] / (top["ms"] / 1e3) / 1e9, 1)}}
+
+
+def sweep_bench(n, mp, reps=8):
+    """Dense Haar k-qubit gates, k = 1..7, on low / high / mixed targets, in
+    each arithmetic mode: GB/s per gate (2 x 2^n x S bytes), % of the measured
+    HBM peak and, on the tensor-core path, the executed 3xTF32 tensor flops
+    against the derived TF32 peak."""
+    import torch
+
+    import paper_2503_19894_gb300 as pkg
+    from paper_2503_19894_gb300 import capi
+    tf32 = mp.get("bf16_tflops_sustained", 1739.5) * 1.1 / 2.25
+    tc0, f640 = capi.cast_get_tensor_mode(), capi.cast_get_f64_mode()
+    out = {}
+    for dtype, mode in (("c64", "fp32"), ("c64", "tf32x3"), ("c128", "double-float"), ("c128", "fp64")):
+        capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3 if mode == "tf32x3" else capi.CAST_TC_OFF)
+        capi.cast_set_f64_mode(capi.CAST_F64_NATIVE if mode == "fp64" else capi.CAST_F64_EMULATED)
+        S = 8 if dtype == "c64" else 16
+        sv = pkg.StateVector(n, dtype, init_index=W.random_basis_index(n, 5))
+        res = {}
+        for k in range(1, 8):
+            r = reps if (S == 8 or k <= 4) else 2
+            row = {}
+            for placement in ("low", "high", "mixed"):
+                gates = W.gate_sweep(n, k, placement, r + 1, 500 + 10 * k + len(placement))
+                sv.apply_gate(gates[0].qubits, gates[0].matrix)  # warm-up
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                capi.cast_profile_begin()
+                e0.record()
+                for g in gates[1:]:
+                    sv.apply_gate(g.qubits, g.matrix)
+                e1.record()
+                torch.cuda.synchronize()
+                prof = capi.cast_profile_end()
+                ms = e0.elapsed_time(e1) / r
+                gbs = 2.0 * (1 << n) * S / (ms / 1e3) / 1e9
+                ent = {"ms": round(ms, 3), "gbs": round(gbs, 1), "hbm_frac": round(gbs / mp["hbm_gbs"], 4),
+                       "kernel": prof[0]["name"] if prof else None}
+                if prof and prof[0]["name"].startswith("tc_"):
+                    ent["tensor_tflops_executed"] = round(3 * 8.0 * (1 << (n + k)) / (ms / 1e3) / 1e12, 1)
+                    ent["tensor_frac_of_derived_tf32"] = round(ent["tensor_tflops_executed"] / tf32, 4)
+                row[placement] = ent
+            res[f"k{k}"] = row
+        sv.close()
+        torch.cuda.empty_cache()
+        out[f"{dtype}_{mode}"] = res
+    capi.cast_set_tensor_mode(tc0)
+    capi.cast_set_f64_mode(f640)
+    return {"n_qubits": n, "gates_per_point": reps, "gates_per_point_c128_k5plus": 2,
+            "tf32_peak_derived": round(tf32, 1), "results": out}
 
 
 def vqa_bench():
@@ -479,6 +532,8 @@ def main():
             line["other_dtype"] = secondary_dtype(n, a.layers, a.max_k, "c128" if S == 8 else "c64")
         if world == 1 and not a.no_vqa:
             line["vqa"] = vqa_bench()
+        if world == 1 and a.sweep:
+            line["sweep"] = sweep_bench(n, mp)
         if world == 1 and not a.no_cpu:
             line["cpu_baseline"] = cpu_baseline(n, qft, a.cpu_seconds)
         print(json.dumps(line), flush=True)

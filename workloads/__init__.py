@@ -177,3 +177,19 @@ def random_state(n, seed):
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
     return v / np.linalg.norm(v)
+
+
+def random_state_device(n, dtype, seed):
+    """Normalised complex Gaussian state of 2^n amplitudes drawn directly on
+    the current CUDA device with torch's seeded generator (for states too
+    large to draw on the host).  dtype: "c64" or "c128"."""
+    import torch
+    real = torch.float32 if dtype == "c64" else torch.float64
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(seed))
+    re = torch.randn(1 << n, generator=g, device="cuda", dtype=real)
+    im = torch.randn(1 << n, generator=g, device="cuda", dtype=real)
+    psi = torch.complex(re, im)
+    del re, im
+    psi /= torch.linalg.vector_norm(psi)
+    return psi
