@@ -8,32 +8,49 @@
 //     Y^T (128 x 2^(k+1)) = X^T (128 x 2^(k+1)) * W^T,
 // one tcgen05.mma chain with M = 128 (TMEM lane = slice), N = K = 2^(k+1).
 //
-// Precision: 3xTF32.  Each operand x is split into hi = tf32(x) and
-// lo = tf32(x - hi), both rounded to nearest; the three products lo*W_hi +
-// hi*W_lo + hi*W_hi are accumulated in fp32 in TMEM, giving fp32-class
-// accuracy (the dropped lo*lo term and the rounding of lo are ~2^-22
-// relative).  Rounding lo (rather than letting the tensor cores truncate it)
-// removes one bias.  The tensor cores' fp32 accumulation itself truncates
-// toward zero, which shrinks every output slightly (measured: ~2^-23 of the
-// norm per gate, growing with k).  A unitary gate preserves the norm of every
-// slice exactly, so each slice's outputs are rescaled by |x| / |y| (both norms
-// summed with a compensated fp32 pair); what remains is unbiased rounding
-// noise.  The correction is applied as y + y * delta with delta formed as a
-// small number, so it is not quantised to the fp32 spacing near 1.  Only gates
-// that are unitary to 1e-9 take this path.
+// Precision: 3xTF32.  Each state operand x is split into hi = x with its 13
+// low significand bits cleared (exactly representable in tf32) and lo =
+// tf32(x - hi) rounded to nearest (the subtraction is exact); the gate is
+// split as W_hi = tf32(W), W_lo = tf32(W - W_hi), both rounded.  The three
+// products lo*W_hi + hi*W_lo + hi*W_hi are accumulated in fp32 in TMEM, giving
+// fp32-class accuracy (the dropped lo*lo term and the rounding of lo are
+// ~2^-21 relative).  Rounding lo (rather than letting the tensor cores
+// truncate it) removes one bias.  The tensor cores' fp32 accumulation itself
+// truncates toward zero, which shrinks every output slightly (measured:
+// ~2^-23 of the norm per gate, growing with k).  A unitary gate preserves the
+// norm of every slice exactly, so each slice's outputs are rescaled by
+// |x| / |y|.  Both norms are plain fp32 sums: their rounding errors are
+// unbiased and average out over slices and gates, while the truncation they
+// correct is systematic; what remains is unbiased rounding noise.  The
+// correction is applied as y + y * delta with delta formed as a small number,
+// so it is not quantised to the fp32 spacing near 1.  Only gates that are
+// unitary to 1e-9 take this path.
 //
 // Data path per tile: thread (warp w, lane i) owns slice 32*(w%4) + i, i.e.
-// TMEM lane 32*(w%4) + i, and 16 of its members (warp group w/4).  It gathers
-// them from HBM with the Eq. 4 addressing (for a fixed member, 32 lanes read 32
-// consecutive slices), splits hi/lo in registers and writes both into TMEM
-// with tcgen05.st: the state tile never passes through shared memory.  The
-// MMAs read A from TMEM and W_hi / W_lo from shared memory (128-byte swizzled
-// K-major, built once per CTA from the hi/lo split of U carried in the launch
-// parameters).  The next tile's loads are issued before the MMAs are waited
-// for, so they stay in flight through the MMAs and the epilogue.
-// TMEM per CTA: accumulator, A_hi, A_lo = 3 x 2^(k+1) columns (rounded up to a
-// power of two); registers and padding of the shared-memory request keep the
-// number of resident CTAs per SM within the 512 TMEM columns.
+// TMEM lane 32*(w%4) + i, and 16 of its members (warp group w/4).  A warp's
+// 32 slices x 16 members form a cube of 9 index bits (the 5 lowest non-target
+// bits and the targets q0..q3); bits 0..3 are always among them, so the cube
+// is made of runs of at least 16 contiguous amplitudes (128 bytes).  The warp
+// reads it with coalesced 16-byte loads in address order, parks it in its own
+// 4 KB of shared memory and every thread then reads its slice row from there;
+// outputs go back the same way.  For k <= 5 the loads are cp.async copies
+// into a ring of two such buffers per warp, so two tiles are in flight while
+// one is computed; k = 6 prefetches one tile into registers.  The buffer is
+// XOR-swizzled per gate (host-built tables): a cube element c sits in slot
+// c ^ X(c >> 4), with X mapping the row bits that land above bit 3 onto free
+// slot bits 1..3, so that the 16-byte chunk accesses (8 lanes per phase) are
+// conflict-free and the 8-byte row accesses (16 lanes per phase) are too,
+// except for a 2-way conflict when qubit 0 is a target.  Rows are split hi/lo in registers and written into TMEM with
+// tcgen05.st.  The MMAs read A from TMEM and W_hi / W_lo from shared memory
+// (128-byte swizzled K-major, built once per CTA from the hi/lo split of U
+// carried in the launch parameters).
+// Pipeline: two accumulators alternate between tiles.  While the MMAs of tile
+// t run, the threads drain tile t-1's accumulator (norm fix, stores), and the
+// loads of tile t+1 are already in flight (issued right after tile t's
+// operands went into TMEM).
+// TMEM per CTA: two accumulators, A_hi, A_lo = 4 x 2^(k+1) columns (128, 256,
+// 512 for k = 4, 5, 6); registers and padding of the shared-memory request
+// keep the number of resident CTAs per SM within the 512 TMEM columns.
 //
 // Waits on the mbarrier are bounded; a CTA that gives up sets an error bit in
 // g_tc_error (read by the host at its next synchronisation point), stops its
@@ -86,18 +103,47 @@ struct TcShape {
     static constexpr int MPT = D < 16 ? D : 16;  // members per thread
     static constexpr int GROUPS = D / MPT;     // warps per TMEM lane quarter
     static constexpr int NT = 128 * GROUPS;    // threads per CTA
-    static constexpr int NCOL = 3 * NK <= 128 ? 128 : (3 * NK <= 256 ? 256 : 512);
+    static constexpr int NCOL = 4 * NK;        // two accumulators, A_hi, A_lo
     static constexpr int CTAS_PER_SM = 512 / NCOL;
+    // staging cubes per warp: k <= 5 keeps a ring of two filled by cp.async
+    // (two tiles in flight); k = 6 (128 KB of W in shared memory) keeps one
+    // and prefetches the next tile into registers
+    static constexpr int STAGES = K <= 5 ? 2 : 1;
+    static_assert(NCOL >= 128 && NCOL <= 512, "TMEM columns");
+};
+
+// tf32 parts of an fp32 value with integer operations: the value with its 13
+// low significand bits cleared (exact in tf32), and the nearest tf32 value
+// (ties away from zero, as cvt.rna; the carry into the exponent is the
+// correct rounding).
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Per-gate tables of a warp's 9-bit cube (see the header): global offsets
+// (in amplitudes, relative to the warp's cube base) and swizzled shared slots.
+// slot() and the offsets are additive over disjoint bit fields, so an element
+// is addressed by combining one per-lane and one per-round entry.
+struct TcStage {
+    uint64_t g_lane[32];  // offset of cube element 2 * lane (a 16-byte chunk)
+    uint64_t g_j[8];      // offset of cube element 64 * j (chunk round j)
+    uint16_t s_lane[32];  // slot of element 2 * lane
+    uint16_t s_j[8];      // slot of element 64 * j
+    uint16_t s_row[32];   // slot of (slice row r, member 0), r = lane
+    uint16_t s_mem[16];   // slot of (row 0, member m)
 };
 
 template <int K>
 __global__ void __launch_bounds__(TcShape<K>::NT, TcShape<K>::CTAS_PER_SM)
 k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-           const __grid_constant__ TcMat<K> U, uint32_t wait_limit, int skip_mma) {
+           const __grid_constant__ TcMat<K> U, const __grid_constant__ TcStage st, uint32_t wait_limit,
+           int skip_mma) {
     using S = TcShape<K>;
     constexpr int NK = S::NK, MPT = S::MPT;
     constexpr uint32_t IDESC = tc::idesc_tf32(128, NK);
-    constexpr uint32_t COL_AH = NK, COL_AL = 2 * NK;
+    constexpr int G = S::GROUPS;
+    constexpr uint32_t COL_AH = NK, COL_AL = 2 * NK, COL_ACC1 = 3 * NK;  // accumulator 0 at column 0
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -105,8 +151,8 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     uint8_t *sWlo = sWhi + NK * NK * 4;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sWlo + NK * NK * 4);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
-    float2 *xnorm = reinterpret_cast<float2 *>(tslot + 2);   // [GROUPS][128] compensated |x|^2 parts
-    float2 *ynorm = xnorm + S::GROUPS * 128;                 // [GROUPS][128] compensated |y|^2 parts
+    float *xnorm = reinterpret_cast<float *>(tslot + 2);  // [2][GROUPS][128] |x|^2 parts of a row
+    float *ynorm = xnorm + 2 * G * 128;                   // [GROUPS][128] |y|^2 parts
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quarter = warp & 3, group = warp >> 2, j0 = group * MPT;
@@ -132,64 +178,165 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     const uint32_t taddr = *tslot;
     const uint32_t lane_addr = taddr + (uint32_t(32 * quarter) << 16);
 
-    // offsets of this thread's members relative to the slice base
-    uint64_t p[K];
-#pragma unroll
-    for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
+    // this warp's staging cubes (STAGES x 512 amplitudes), after the norm arrays
+    constexpr int NS = S::STAGES;
+    float2 *stages = reinterpret_cast<float2 *>(ynorm + G * 128 + 4) + warp * (512 * NS);
+    // member offset of this warp group's first member j0 (targets q4, q5 only)
     uint64_t off0 = 0;
 #pragma unroll
-    for (int i = 0; i < K; i++)
-        if ((j0 >> i) & 1) off0 += p[i];
-    auto member_off = [&](int m) {  // m compile-time after unrolling
-        uint64_t o = off0;
+    for (int i = 4; i < K; i++)
+        if ((j0 >> i) & 1) off0 += uint64_t(1) << tg.q[i];
+    const uint64_t g_lane = st.g_lane[lane];
+    const uint32_t s_lane = st.s_lane[lane], s_row = st.s_row[lane];
+    auto cube_base = [&](uint64_t t) { return slice_base<K>(t * 128 + uint64_t(32 * quarter), tg) + off0 + g_lane; };
+    // the warp's cube of tile t, 8 chunks of 16 bytes per lane, coalesced
+    auto copy_async = [&](uint64_t t, float2 *stage) {
+        const float2 *b = sv + cube_base(t);
+        const uint32_t d = tc::smem_u32(stage);
 #pragma unroll
-        for (int i = 0; i < K; i++)
-            if ((m >> i) & 1) o += p[i];
-        return o;
+        for (int j = 0; j < 8; j++)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ st.s_j[j]) >> 1) * 16u),
+                         "l"(b + st.g_j[j])
+                         : "memory");
     };
-    auto load = [&](uint64_t tile, float2 (&x)[MPT]) {
-        const uint64_t b = slice_base<K>(tile * 128 + uint64_t(32 * quarter + lane), tg);
+    auto load_regs = [&](uint64_t t, float4 (&c)[8]) {
+        const float2 *b = sv + cube_base(t);
 #pragma unroll
-        for (int m = 0; m < MPT; m++) x[m] = sv[b + member_off(m)];
+        for (int j = 0; j < 8; j++) c[j] = __ldcs(reinterpret_cast<const float4 *>(b + st.g_j[j]));
+    };
+    auto regs_to_stage = [&](const float4 (&c)[8], float2 *stage) {
+        float4 *s4 = reinterpret_cast<float4 *>(stage);
+#pragma unroll
+        for (int j = 0; j < 8; j++) s4[(s_lane ^ st.s_j[j]) >> 1] = c[j];
     };
 
-    float2 cur[MPT], nxt[MPT];
-    uint64_t tile = blockIdx.x;
+    // drain one tile's accumulator: restore each slice's norm, store to HBM
+    // through the staging cube `stage` (free: its input is already in TMEM).
+    // xh, xl: this thread's compensated |x|^2 of the tile (GROUPS == 1), else
+    // the parts every warp group left in xnorm[xb]
+    auto epilogue = [&](uint64_t t, uint32_t acc_col, int xb, float xrow, float2 *stage) {
+        float Y = 0.f, Y2 = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {  // pass 1: |y|^2 of the row
+            float v[MPT];
+            tc::tmem_ld<MPT>(lane_addr + acc_col + 2 * j0 + MPT * h, v);
+#pragma unroll
+            for (int m = 0; m < MPT / 2; m++) {
+                Y = fmaf(v[2 * m], v[2 * m], Y);
+                Y2 = fmaf(v[2 * m + 1], v[2 * m + 1], Y2);
+            }
+        }
+        Y += Y2;
+        float X = xrow;
+        if constexpr (G > 1) {
+            // the row's members are spread over the G warps of this lane quarter
+            ynorm[group * 128 + row] = Y;
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(32 * G) : "memory");
+            X = 0.f;
+            Y = 0.f;
+#pragma unroll
+            for (int gq = 0; gq < G; gq++) {
+                X += xnorm[(xb * G + gq) * 128 + row];
+                Y += ynorm[gq * 128 + row];
+            }
+        }
+        // y <- y * sqrt(X / Y) = y + y * delta with delta = (X - Y) / (2 Y) to
+        // first order (|delta| ~ 1e-7; the second-order term is ~1e-14).
+        // delta is formed as a small number (X - Y is exact when the two are
+        // close) so the correction is not quantised to multiples of 2^-23 as
+        // a scale factor near 1 would be.
+        float delta = 0.0f;
+        if (Y > 0.0f && X > 0.0f) delta = 0.5f * (X - Y) / Y;
+        // pass 2: corrected row -> staging cube -> coalesced 16-byte stores
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            float v[MPT];
+            tc::tmem_ld<MPT>(lane_addr + acc_col + 2 * j0 + MPT * h, v);
+#pragma unroll
+            for (int m = 0; m < MPT / 2; m++)
+                stage[s_row ^ st.s_mem[h * (MPT / 2) + m]] =
+                    make_float2(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1]));
+        }
+        __syncwarp();
+        float2 *b = sv + cube_base(t);
+        const float4 *s4 = reinterpret_cast<const float4 *>(stage);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            __stcs(reinterpret_cast<float4 *>(b + st.g_j[j]), s4[(s_lane ^ st.s_j[j]) >> 1]);
+        __syncwarp();
+    };
+
+    float4 nxt[8];  // register prefetch (one stage only)
+    const uint64_t step = gridDim.x;
+    uint64_t tile = blockIdx.x, prev = ~uint64_t(0);
     uint32_t phase = 0;
+    int buf = 0;  // accumulator (and xnorm half) of the current tile
+    float x_prev = 0.f;
     bool failed = false;
-    if (tile < ntiles) load(tile, cur);
+    if constexpr (NS > 1) {
+#pragma unroll
+        for (int si = 0; si < NS; si++) {
+            if (tile + si * step < ntiles) copy_async(tile + si * step, stages + si * 512);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+    } else {
+        if (tile < ntiles) load_regs(tile, nxt);
+    }
+    int si = 0;  // stage of the current tile
     while (tile < ntiles) {
-        // ---- split, TMEM stores of A_hi and A_lo (this thread's row, its members)
-        float v[2 * MPT];
-#pragma unroll
-        for (int m = 0; m < MPT; m++) {
-            v[2 * m] = tc::to_tf32(cur[m].x);
-            v[2 * m + 1] = tc::to_tf32(cur[m].y);
+        float2 *stage = stages + si * 512;
+        // ---- this thread's slice row from the staged cube
+        if constexpr (NS > 1) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+        } else {
+            regs_to_stage(nxt, stage);
         }
-        tc::tmem_st<2 * MPT>(lane_addr + COL_AH + 2 * j0, v);
-        // the remainder is rounded to tf32 as well: the tensor cores would
-        // otherwise truncate it, a bias that shrinks the norm gate after gate
+        __syncwarp();
+        // ---- split in two halves of 8 members, TMEM stores of A_hi and A_lo
+        // (the previous MMAs are done)
+        float xs = 0.f, xs2 = 0.f;
 #pragma unroll
-        for (int m = 0; m < MPT; m++) {
-            v[2 * m] = tc::to_tf32(cur[m].x - v[2 * m]);
-            v[2 * m + 1] = tc::to_tf32(cur[m].y - v[2 * m + 1]);
-        }
-        tc::tmem_st<2 * MPT>(lane_addr + COL_AL + 2 * j0, v);
-        {
-            Acc<float> xs;
+        for (int h = 0; h < 2; h++) {
+            float2 x[MPT / 2];
 #pragma unroll
-            for (int m = 0; m < MPT; m++) xs.add(cur[m].x * cur[m].x + cur[m].y * cur[m].y);
-            xnorm[group * 128 + row] = make_float2(xs.hi, xs.lo);
+            for (int m = 0; m < MPT / 2; m++) x[m] = stage[s_row ^ st.s_mem[h * (MPT / 2) + m]];
+            float v[MPT];
+#pragma unroll
+            for (int m = 0; m < MPT / 2; m++) {
+                v[2 * m] = tf32_trunc(x[m].x);
+                v[2 * m + 1] = tf32_trunc(x[m].y);
+            }
+            tc::tmem_st<MPT>(lane_addr + COL_AH + 2 * j0 + MPT * h, v);
+            // the remainder is rounded to tf32 as well: the tensor cores would
+            // otherwise truncate it, a bias that shrinks the norm gate after gate
+#pragma unroll
+            for (int m = 0; m < MPT / 2; m++) {
+                v[2 * m] = tf32_round(x[m].x - v[2 * m]);
+                v[2 * m + 1] = tf32_round(x[m].y - v[2 * m + 1]);
+            }
+            tc::tmem_st<MPT>(lane_addr + COL_AL + 2 * j0 + MPT * h, v);
+#pragma unroll
+            for (int m = 0; m < MPT / 2; m++) {
+                xs = fmaf(x[m].x, x[m].x, xs);
+                xs2 = fmaf(x[m].y, x[m].y, xs2);
+            }
         }
+        xs += xs2;
+        if constexpr (G > 1) xnorm[(buf * G + group) * 128 + row] = xs;
         tc::tmem_wait_st();
-        // ---- prefetch the next tile; the loads stay in flight meanwhile
-        const uint64_t next = tile + gridDim.x;
-        if (next < ntiles) load(next, nxt);
+        const uint64_t next = tile + step;
+        if constexpr (NS == 1) {  // prefetch the next tile; in flight meanwhile
+            if (next < ntiles) load_regs(next, nxt);
+        }
         tc::fence_before_sync();
-        __syncthreads();
+        // every row is in TMEM; a failed wait of the previous tile ends the
+        // loop here, agreed by all threads
+        if (__syncthreads_or(failed)) break;
         tc::fence_after_sync();
         if (tid == 0 && !skip_mma) {
             const uint32_t wH = tc::smem_u32(sWhi), wL = tc::smem_u32(sWlo);
+            const uint32_t dacc = taddr + (buf ? COL_ACC1 : 0u);
             uint32_t acc = 0;
 #pragma unroll
             for (int pr = 0; pr < 3; pr++) {
@@ -198,55 +345,34 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
 #pragma unroll
                 for (int s = 0; s < NK / 8; s++) {
                     const uint32_t kw = uint32_t((s >> 2) * (NK / 8) * 1024 + (s & 3) * 32);
-                    tc::mma_tf32_ts(taddr, taddr + acol + 8 * s, tc::smem_desc_sw128(w + kw), IDESC, acc);
+                    tc::mma_tf32_ts(dacc, taddr + acol + 8 * s, tc::smem_desc_sw128(w + kw), IDESC, acc);
                     acc = 1;
                 }
             }
             tc::mma_commit(mbar);
         }
-        const bool ok = tc::mbar_wait(mbar, phase, wait_limit);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+        __syncwarp();  // warp 0 reconverges before its .sync.aligned TMEM loads
+        // ---- the previous tile's epilogue runs while these MMAs execute; it
+        // stores through this tile's staging cube, which is then refilled
+        if (prev != ~uint64_t(0)) epilogue(prev, buf ? 0u : COL_ACC1, buf ^ 1, x_prev, stage);
+        if constexpr (NS > 1) {
+            __syncwarp();
+            if (tile + NS * step < ntiles) copy_async(tile + NS * step, stage);
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        x_prev = xs;
+        failed = !tc::mbar_wait(mbar, phase, wait_limit);
         phase ^= 1u;
         tc::fence_after_sync();
-        // ---- accumulator -> registers; restore the slice norm; -> HBM
-        tc::tmem_ld<2 * MPT>(lane_addr + 2 * j0, v);
-        {
-            Acc<float> ys;
-#pragma unroll
-            for (int m = 0; m < MPT; m++) ys.add(v[2 * m] * v[2 * m] + v[2 * m + 1] * v[2 * m + 1]);
-            ynorm[group * 128 + row] = make_float2(ys.hi, ys.lo);
-        }
-        __syncthreads();
-        {
-            Acc<float> X, Y;
-#pragma unroll
-            for (int gq = 0; gq < S::GROUPS; gq++) {
-                const float2 a = xnorm[gq * 128 + row], b = ynorm[gq * 128 + row];
-                X.add(a.x); X.add(a.y);
-                Y.add(b.x); Y.add(b.y);
-            }
-            // y <- y * sqrt(X / Y) = y + y * delta with delta = (X - Y) / (2 Y) to
-            // first order (|delta| ~ 1e-7; the second-order term is ~1e-14).
-            // delta is formed as a small number (X.hi - Y.hi is exact when the
-            // two are close) so the correction keeps full fp32 precision; a
-            // scale factor near 1 would be quantised to multiples of 2^-23.
-            float delta = 0.0f;
-            if (Y.hi > 0.0f && X.hi > 0.0f) delta = 0.5f * ((X.hi - Y.hi) + (X.lo - Y.lo)) / Y.hi;
-            const uint64_t b = slice_base<K>(tile * 128 + uint64_t(row), tg);
-#pragma unroll
-            for (int m = 0; m < MPT; m++)
-                __stcs(&sv[b + member_off(m)],
-                       make_float2(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1])));
-        }
+        prev = tile;
         tile = next;
-#pragma unroll
-        for (int m = 0; m < MPT; m++) cur[m] = nxt[m];
-        tc::fence_before_sync();
-        __syncthreads();
+        buf ^= 1;
+        si = (si + 1) % NS;
     }
+    if constexpr (NS > 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    failed = __syncthreads_or(failed);
+    if (failed) phase ^= 1u;  // the wait that ran out is retried below
+    if (!failed && prev != ~uint64_t(0)) epilogue(prev, buf ? 0u : COL_ACC1, buf ^ 1, x_prev, stages + si * 512);
     if (failed) {
         if (tid == 0) atomicOr(&g_tc_error, 1);
         tc::mbar_wait(mbar, phase, wait_limit);  // let an MMA in flight finish before freeing TMEM
@@ -270,10 +396,83 @@ float host_tf32(float x) {
 template <int K>
 size_t tc_smem_bytes() {
     using S = TcShape<K>;
-    const size_t need = 1024 + size_t(S::NK) * S::NK * 4 * 2 + 64 + 2 * 8 * 128 * S::GROUPS;
+    const size_t need = 1024 + size_t(S::NK) * S::NK * 4 * 2 + 64 + 3 * 4 * 128 * S::GROUPS + 16 +
+                        size_t(S::NT / 32) * 4096 * S::STAGES;
     // at most CTAS_PER_SM resident CTAs per SM (228 KB of shared memory each)
     const size_t floor = (228 * 1024) / (S::CTAS_PER_SM + 1) + 1024;
     return need > floor ? need : floor;
+}
+
+// Staging tables for sorted targets q[0..k): the warp cube's 9 address bits
+// are the 5 lowest non-target bits (the row bits r0..r4) and q0..q3 (the
+// member bits m0..m3), in ascending order; cube position b holds address bit
+// abit[b].  The swizzle X sends each of r0..r3 that sits at position >= 4 to
+// a low slot bit that no row bit occupies, so that the 16 rows of a half-warp
+// land in different 8-byte bank pairs.
+TcStage make_stage(const int *q, int k) {
+    int rpos[5], mpos[4], abit[9];
+    int nr = 0, nm = 0, nb = 0;
+    for (int a = 0; nb < 9; a++) {
+        bool target = false;
+        int ti = -1;
+        for (int i = 0; i < k; i++)
+            if (q[i] == a) {
+                target = true;
+                ti = i;
+            }
+        if (target && ti < 4) {
+            mpos[nm++] = nb;
+            abit[nb++] = a;
+        } else if (!target && nr < 5) {
+            rpos[nr++] = nb;
+            abit[nb++] = a;
+        }
+    }
+    // X touches slot bits 1..3 only, so a 16-byte chunk (elements 2i, 2i+1)
+    // stays whole and in order (cp.async copies it as is).  When bit 0 is a
+    // target, four row bits share three slot bits: a 2-way conflict remains.
+    uint32_t contrib[9] = {0};
+    uint32_t used = 1u;
+    for (int h = 0; h < 4; h++)
+        if (rpos[h] < 4) used |= 1u << rpos[h];
+    int next_free = 1;
+    for (int h = 0; h < 4; h++)
+        if (rpos[h] >= 4) {
+            while (next_free < 4 && (used & (1u << next_free))) next_free++;
+            if (next_free >= 4) break;
+            contrib[rpos[h]] = 1u << next_free;
+            used |= 1u << next_free;
+        }
+    auto slot = [&](uint32_t c) {
+        uint32_t x = c;
+        for (int b = 4; b < 9; b++)
+            if ((c >> b) & 1) x ^= contrib[b];
+        return uint16_t(x);
+    };
+    auto goff = [&](uint32_t c) {
+        uint64_t o = 0;
+        for (int b = 0; b < 9; b++)
+            if ((c >> b) & 1) o += uint64_t(1) << abit[b];
+        return o;
+    };
+    auto deposit = [&](uint32_t v, const int *pos, int cnt) {
+        uint32_t c = 0;
+        for (int i = 0; i < cnt; i++)
+            if ((v >> i) & 1) c |= 1u << pos[i];
+        return c;
+    };
+    TcStage st;
+    for (int i = 0; i < 32; i++) {
+        st.g_lane[i] = goff(2u * i);
+        st.s_lane[i] = slot(2u * i);
+        st.s_row[i] = slot(deposit(i, rpos, 5));
+    }
+    for (int j = 0; j < 8; j++) {
+        st.g_j[j] = goff(64u * j);
+        st.s_j[j] = slot(64u * j);
+    }
+    for (int m = 0; m < 16; m++) st.s_mem[m] = slot(deposit(m, mpos, 4));
+    return st;
 }
 
 template <int K>
@@ -309,7 +508,8 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     ProfScope ps(sv->stream, "tc_k" + std::to_string(K) + "_c64", 16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
     const uint32_t inject = g_inject_limit.exchange(0);
-    k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U,
+    const TcStage st = make_stage(g.q, K);
+    k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
                                                                inject ? inject : kWaitLimit, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;

@@ -318,6 +318,30 @@ def test_tensor_core_fused_circuit(tensor_mode):
     sv.close()
 
 
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_tensor_core_norm_does_not_drift(k, tensor_mode):
+    """400 Haar k-qubit gates on the tensor cores: the per-slice norm
+    restoration leaves unbiased noise, so the norm stays at 1 (a bias of the
+    size of the tensor cores' truncation, ~2^-23 per gate, would move it by
+    ~1e-4) and the state stays within the complex64 bound of the oracle."""
+    capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
+    n = 17
+    rng = np.random.default_rng(900 + k)
+    gates = [W.Gate("U", W.sweep_targets(n, k, ("low", "high", "mixed")[i % 3], rng),
+                    matrix=W.haar_unitary(k, rng)) for i in range(400)]
+    psi0 = W.random_state(n, 17)
+    ref = oracle.apply_circuit(psi0.copy(), gates)
+    sv = pkg.StateVector(n, "c64", init_index=None)
+    sv.from_numpy(psi0.astype(np.complex64))
+    sv.apply_circuit(gates, fusion="none")
+    assert abs(sv.expectation([W.PauliTerm(1.0, "", ())]) - 1.0) <= 1e-5
+    got = sv.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= TOL["c64"]
+    # relative to the state, the error is a random walk of fp32-sized steps
+    assert np.linalg.norm(got - ref) <= 2e-5
+    sv.close()
+
+
 def test_tensor_mode_validation(tensor_mode):
     with pytest.raises(capi.CastError):
         capi.cast_set_tensor_mode(7)
