@@ -7,6 +7,13 @@
 //                      in the launch's parameter space (<= 16 KB) so every
 //                      thread reads the same entry from the constant bank in
 //                      lockstep (broadcast).
+//   k_dense_cube<K>    complex64, K <= 4, gates with two or more low targets:
+//                      the same matvec per slice, but each warp moves its 32
+//                      slices as one staged cube (struct CubeTables):
+//                      coalesced 16-byte cp.async chunks into a ring of two
+//                      swizzled shared-memory buffers, the slice rows read
+//                      from there, the outputs written back through the same
+//                      buffer.
 //   k_dense_tile<R,K>  K = 6, 7.  A CTA stages 2^K x TS amplitudes in shared
 //                      memory, then each thread forms (row, slice) outputs
 //                      reading the matrix from global memory (L1-resident).
@@ -82,6 +89,70 @@ k_dense(typename Cx<R>::T *__restrict__ sv, uint64_t nslices, Targets tg,
             sv[base + off] = y;
         }
     }
+}
+
+// --------------------------------------------- dense complex64, staged cube
+template <int K>
+constexpr int cube_ctas_per_sm() { return K <= 2 ? 4 : (K == 3 ? 3 : 2); }
+
+template <int K>
+__global__ void __launch_bounds__(256, cube_ctas_per_sm<K>())
+k_dense_cube(float2 *__restrict__ sv, uint64_t ncubes, Targets tg, const __grid_constant__ DenseMat<float, K> U,
+             const __grid_constant__ CubeTables ct) {
+    constexpr int D = 1 << K, E = 32 * D, CH = D / 2, NS = 2;
+    extern __shared__ __align__(16) unsigned char cube_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *stages = reinterpret_cast<float2 *>(cube_smem) + warp * (NS * E);
+    const uint64_t g_lane = ct.g_lane[lane];
+    const uint32_t s_lane = ct.s_lane[lane], s_row = ct.s_row[lane];
+    const uint64_t wstep = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    auto cube_base = [&](uint64_t c) { return slice_base<K>(c * 32, tg) + g_lane; };
+    auto copy_async = [&](uint64_t c, float2 *stage) {
+        const float2 *b = sv + cube_base(c);
+        const uint32_t d = uint32_t(__cvta_generic_to_shared(stage));
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ ct.s_j[j]) >> 1) * 16u),
+                         "l"(b + ct.g_j[j])
+                         : "memory");
+    };
+    uint64_t c = uint64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+#pragma unroll
+    for (int si = 0; si < NS; si++) {
+        if (c + si * wstep < ncubes) copy_async(c + si * wstep, stages + si * E);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int si = 0; c < ncubes; c += wstep, si ^= 1) {
+        float2 *stage = stages + si * E;
+        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+        __syncwarp();
+        float2 x[D];
+#pragma unroll
+        for (int m = 0; m < D; m++) x[m] = stage[s_row ^ ct.s_mem[m]];
+        // the row's slots belong to this lane alone: the outputs go in place
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int cc = 0; cc < D; cc++) {
+                const float2 u = U.m[r][cc];
+                re = fmaf(u.x, x[cc].x, re);
+                re = fmaf(-u.y, x[cc].y, re);
+                im = fmaf(u.x, x[cc].y, im);
+                im = fmaf(u.y, x[cc].x, im);
+            }
+            stage[s_row ^ ct.s_mem[r]] = make_float2(re, im);
+        }
+        __syncwarp();
+        float2 *b = sv + cube_base(c);
+        const float4 *s4 = reinterpret_cast<const float4 *>(stage);
+#pragma unroll
+        for (int j = 0; j < CH; j++) __stcs(reinterpret_cast<float4 *>(b + ct.g_j[j]), s4[(s_lane ^ ct.s_j[j]) >> 1]);
+        __syncwarp();
+        if (c + NS * wstep < ncubes) copy_async(c + NS * wstep, stage);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // --------------------------------------------------------- dense, K = 6, 7
@@ -246,6 +317,31 @@ template <typename R, int K>
 cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
     using T2 = typename Cx<R>::T;
     const uint64_t ns = uint64_t(1) << (sv->n - K);
+    if constexpr (K <= 4 && sizeof(R) == 4) {
+        // Targets below the 5th non-target bit (q_i - i < 5) spread a warp's
+        // 32 slices over 32 x 2^L amplitudes for one member: with L >= 2 the
+        // direct kernel's loads touch 4x the lines they use, and the staged
+        // cube is faster; otherwise the direct kernel is already coalesced.
+        int L = 0;
+        for (int i = 0; i < K; i++) L += (g.q[i] - i) < 5;
+        if (L >= 2 && sv->n >= K + 5) {  // staged cubes of 32 slices
+            DenseMat<float, K> U;
+            for (int r = 0; r < (1 << K); r++)
+                for (int c = 0; c < (1 << K); c++) U.m[r][c] = to_dev<float>(g.m[size_t(r) * (1 << K) + c]);
+            const CubeTables ct = make_cube_tables(g.q, K);
+            const uint64_t ncubes = ns >> 5;
+            const size_t smem = size_t(8) * 2 * 32 * (1 << K) * sizeof(float2);
+            CAST_CUDA(cudaFuncSetAttribute(k_dense_cube<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int per_sm = tuned_blocks_per_sm(sv->dt, K, CLS_DENSE, cube_ctas_per_sm<K>());
+            const uint64_t want = (ncubes + 7) / 8, cap = uint64_t(sm_count_cached()) * per_sm;
+            ProfScope ps(sv->stream, "dense_k" + std::to_string(K) + "_" + dt_name(sv->dt),
+                         2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
+            k_dense_cube<K><<<(unsigned)(want < cap ? want : cap), 256, smem, sv->stream>>>(
+                reinterpret_cast<float2 *>(sv->data), ncubes, tg, U, ct);
+            CAST_CUDA(cudaGetLastError());
+            return CAST_OK;
+        }
+    }
     if constexpr (K <= 5) {
         DenseMat<R, K> U;
         for (int r = 0; r < (1 << K); r++)

@@ -121,23 +121,11 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// Per-gate tables of a warp's 9-bit cube (see the header): global offsets
-// (in amplitudes, relative to the warp's cube base) and swizzled shared slots.
-// slot() and the offsets are additive over disjoint bit fields, so an element
-// is addressed by combining one per-lane and one per-round entry.
-struct TcStage {
-    uint64_t g_lane[32];  // offset of cube element 2 * lane (a 16-byte chunk)
-    uint64_t g_j[8];      // offset of cube element 64 * j (chunk round j)
-    uint16_t s_lane[32];  // slot of element 2 * lane
-    uint16_t s_j[8];      // slot of element 64 * j
-    uint16_t s_row[32];   // slot of (slice row r, member 0), r = lane
-    uint16_t s_mem[16];   // slot of (row 0, member m)
-};
 
 template <int K>
 __global__ void __launch_bounds__(TcShape<K>::NT, TcShape<K>::CTAS_PER_SM)
 k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-           const __grid_constant__ TcMat<K> U, const __grid_constant__ TcStage st, uint32_t wait_limit,
+           const __grid_constant__ TcMat<K> U, const __grid_constant__ CubeTables st, uint32_t wait_limit,
            int skip_mma) {
     using S = TcShape<K>;
     constexpr int NK = S::NK, MPT = S::MPT;
@@ -403,78 +391,6 @@ size_t tc_smem_bytes() {
     return need > floor ? need : floor;
 }
 
-// Staging tables for sorted targets q[0..k): the warp cube's 9 address bits
-// are the 5 lowest non-target bits (the row bits r0..r4) and q0..q3 (the
-// member bits m0..m3), in ascending order; cube position b holds address bit
-// abit[b].  The swizzle X sends each of r0..r3 that sits at position >= 4 to
-// a low slot bit that no row bit occupies, so that the 16 rows of a half-warp
-// land in different 8-byte bank pairs.
-TcStage make_stage(const int *q, int k) {
-    int rpos[5], mpos[4], abit[9];
-    int nr = 0, nm = 0, nb = 0;
-    for (int a = 0; nb < 9; a++) {
-        bool target = false;
-        int ti = -1;
-        for (int i = 0; i < k; i++)
-            if (q[i] == a) {
-                target = true;
-                ti = i;
-            }
-        if (target && ti < 4) {
-            mpos[nm++] = nb;
-            abit[nb++] = a;
-        } else if (!target && nr < 5) {
-            rpos[nr++] = nb;
-            abit[nb++] = a;
-        }
-    }
-    // X touches slot bits 1..3 only, so a 16-byte chunk (elements 2i, 2i+1)
-    // stays whole and in order (cp.async copies it as is).  When bit 0 is a
-    // target, four row bits share three slot bits: a 2-way conflict remains.
-    uint32_t contrib[9] = {0};
-    uint32_t used = 1u;
-    for (int h = 0; h < 4; h++)
-        if (rpos[h] < 4) used |= 1u << rpos[h];
-    int next_free = 1;
-    for (int h = 0; h < 4; h++)
-        if (rpos[h] >= 4) {
-            while (next_free < 4 && (used & (1u << next_free))) next_free++;
-            if (next_free >= 4) break;
-            contrib[rpos[h]] = 1u << next_free;
-            used |= 1u << next_free;
-        }
-    auto slot = [&](uint32_t c) {
-        uint32_t x = c;
-        for (int b = 4; b < 9; b++)
-            if ((c >> b) & 1) x ^= contrib[b];
-        return uint16_t(x);
-    };
-    auto goff = [&](uint32_t c) {
-        uint64_t o = 0;
-        for (int b = 0; b < 9; b++)
-            if ((c >> b) & 1) o += uint64_t(1) << abit[b];
-        return o;
-    };
-    auto deposit = [&](uint32_t v, const int *pos, int cnt) {
-        uint32_t c = 0;
-        for (int i = 0; i < cnt; i++)
-            if ((v >> i) & 1) c |= 1u << pos[i];
-        return c;
-    };
-    TcStage st;
-    for (int i = 0; i < 32; i++) {
-        st.g_lane[i] = goff(2u * i);
-        st.s_lane[i] = slot(2u * i);
-        st.s_row[i] = slot(deposit(i, rpos, 5));
-    }
-    for (int j = 0; j < 8; j++) {
-        st.g_j[j] = goff(64u * j);
-        st.s_j[j] = slot(64u * j);
-    }
-    for (int m = 0; m < 16; m++) st.s_mem[m] = slot(deposit(m, mpos, 4));
-    return st;
-}
-
 template <int K>
 cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     constexpr int D = 1 << K;
@@ -508,7 +424,7 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     ProfScope ps(sv->stream, "tc_k" + std::to_string(K) + "_c64", 16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
     const uint32_t inject = g_inject_limit.exchange(0);
-    const TcStage st = make_stage(g.q, K);
+    const CubeTables st = make_cube_tables(g.q, K);
     k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
                                                                inject ? inject : kWaitLimit, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());

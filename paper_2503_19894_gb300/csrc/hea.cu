@@ -242,15 +242,79 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
     }
 }
 
+// The same round with the NB rotated bits B0 .. B0+NB-1 fixed at compile
+// time.  The swizzle is linear over disjoint bits (sw(a | b) = sw(a) ^ sw(b)),
+// so each member's slot is the sub-slice's slot XOR a constant.
+template <typename R, int B0, int NB>
+__device__ void tile_round_ct(typename Cx<R>::T *tile, int T0, const Rot<R> *rot) {
+    using T2 = typename Cx<R>::T;
+    const uint32_t nsub = 1u << (T0 - NB);
+    for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
+        const uint32_t sb = sw(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
+        T2 v[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) v[j] = tile[sb ^ sw(uint32_t(j) << B0)];
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            const Rot<R> ri = rot[i];
+#pragma unroll
+            for (int j = 0; j < (1 << NB); j++)
+                if (!((j >> i) & 1)) fwd_pair(v[j], v[j | (1 << i)], ri);
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) tile[sb ^ sw(uint32_t(j) << B0)] = v[j];
+    }
+}
+
+// A thread's loaded share of a tile (local index l = threadIdx.x + 256 i)
+// holds complete sub-slices over local bits 8 .. 8 + log2(IT) - 1, so the RY
+// gates on those bits are applied in registers before the tile is parked.
+template <typename R> constexpr int reg_bits() { return tile_bits<R>() - 8; }
+
+template <typename R, typename Regs>
+__device__ __forceinline__ void reg_rotations(Regs &b, const Geo &G, const Rot<R> *rots) {
+    constexpr int IT = 1 << reg_bits<R>();
+#pragma unroll
+    for (int rb = 0; rb < reg_bits<R>(); rb++) {
+        const int lb = 8 + rb;
+        if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+        const Rot<R> r = rots[G.q0 + lb - G.rb0];
+        const int nact = 1 << (G.T0 - 8);  // registers holding amplitudes
+#pragma unroll
+        for (int i = 0; i < IT; i++)
+            if (!((i >> rb) & 1) && i < nact) fwd_pair(b.v[i], b.v[i | (1 << rb)], r);
+    }
+}
+
+// The RY gates of the rotated bits below 8 (those above were applied in
+// registers): fixed rounds for the full-width groups, else rounds of three
+// with runtime bit positions.
 template <typename R>
-__device__ void apply_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot<R> *rots /* per qubit of layer */) {
-    for (int r0 = 0; r0 < G.nrot; r0 += 3) {
-        const int nb = G.nrot - r0 < 3 ? G.nrot - r0 : 3;
+__device__ void smem_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot<R> *rots) {
+    const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
+    if (G.rb0 >= hi) return;
+    const Rot<R> *r = rots + G.q0;  // RY/RZ entries of the group's rotated qubits, in order
+    if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
+        tile_round_ct<R, 0, 3>(tile, G.T0, r);
+        __syncthreads();
+        tile_round_ct<R, 3, 3>(tile, G.T0, r + 3);
+        __syncthreads();
+        tile_round_ct<R, 6, 2>(tile, G.T0, r + 6);
+        __syncthreads();
+        return;
+    }
+    if (G.rb0 == 5 && hi == 8) {
+        tile_round_ct<R, 5, 3>(tile, G.T0, r);
+        __syncthreads();
+        return;
+    }
+    for (int b0 = G.rb0; b0 < hi; b0 += 3) {
+        const int nb = hi - b0 < 3 ? hi - b0 : 3;
         int bits[3];
         Rot<R> rr[3];
         for (int i = 0; i < nb; i++) {
-            bits[i] = G.rb0 + r0 + i;
-            rr[i] = rots[G.q0 + r0 + i];
+            bits[i] = b0 + i;
+            rr[i] = rots[G.q0 + b0 - G.rb0 + i];
         }
         if (nb == 3) tile_round<R, 3>(tile, G.T0, bits, rr);
         else if (nb == 2) tile_round<R, 2>(tile, G.T0, bits, rr);
@@ -310,11 +374,21 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
     tile_load<R>(buf, arena + I.off, G, t);
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
         const uint32_t sz = 1u << G.T0;
+        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
+        reg_rotations<R>(buf, G, lr);
         tile_put<R>(buf, tile, sz);
-        __syncthreads();
         const HeaInst Ic = I;
         const Geo Gc = G;
         const uint64_t tc = t;
+        // the phase tables depend on the instance only (the tile list of an
+        // instance starts at prefix = gt - tc); rebuilt when it changes
+        const int inst_id = int(gt - tc);
+        if (inst_id != table_inst) {
+            __syncthreads();  // the previous tile's stores read the old tables
+            build_phase_tables<R>(ph0, ph1, Gc, lr);
+            table_inst = inst_id;
+        }
+        __syncthreads();
         if (gt + 1 < t_end) {
             k = find_inst(P, gt + 1);
             I = insts[P.inst[k]];
@@ -322,16 +396,7 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
             t = gt + 1 - P.prefix[k];
             tile_load<R>(buf, arena + I.off, G, t);
         }
-        const Rot<R> *lr = rot + Ic.rot_off + size_t(P.layer) * Ic.n;
-        // the phase tables depend on the instance only (the tile list of an
-        // instance starts at prefix = gt - tc); rebuilt when it changes and
-        // published by the barrier after the first rotation round
-        const int inst_id = int(gt - tc);
-        if (inst_id != table_inst) {
-            build_phase_tables<R>(ph0, ph1, Gc, lr);
-            table_inst = inst_id;
-        }
-        apply_rotations<R>(tile, Gc, lr);
+        smem_rotations<R>(tile, Gc, lr);
         const bool last = P.group == Ic.ngroups - 1;
         T2 *sv = arena + Ic.off;
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
@@ -527,6 +592,48 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
     }
 }
 
+// One RY_q pair of psi and lam in the backward sweep: the pair's share of
+// dE/dtheta_q = Im<lam|Y_q|psi> (Y psi = (-i p1, i p0)), then RY(-theta) on both.
+template <typename T2, typename R>
+__device__ __forceinline__ R adj_pair(T2 &p0, T2 &p1, T2 &l0, T2 &l1, const Rot<R> &r) {
+    const R g = (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
+    ry(p0, p1, r.cy, -r.sy);
+    ry(l0, l1, r.cy, -r.sy);
+    return g;
+}
+
+// adj_round with the NB bits B0 .. B0+NB-1 fixed at compile time (see
+// tile_round_ct for the addressing)
+template <typename R, int B0, int NB>
+__device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, const Rot<R> *rot,
+                             Acc<R> (&gy)[3]) {
+    using T2 = typename Cx<R>::T;
+    const uint32_t nsub = 1u << (T0 - NB);
+    for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
+        const uint32_t sb = sw(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
+        T2 p[1 << NB], l[1 << NB];
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            p[j] = tp[sb ^ sw(uint32_t(j) << B0)];
+            l[j] = tl[sb ^ sw(uint32_t(j) << B0)];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; i++) {
+            const Rot<R> r = rot[i];
+            R sy = 0;
+#pragma unroll
+            for (int j = 0; j < (1 << NB); j++)
+                if (!((j >> i) & 1)) sy += adj_pair(p[j], p[j | (1 << i)], l[j], l[j | (1 << i)], r);
+            gy[i].add(sy);
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << NB); j++) {
+            tp[sb ^ sw(uint32_t(j) << B0)] = p[j];
+            tl[sb ^ sw(uint32_t(j) << B0)] = l[j];
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
 k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
@@ -578,72 +685,133 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
         const uint64_t t = gt - P.prefix[k];
         const uint32_t sz = 1u << G.T0;
         const bool last = P.group == I.ngroups - 1;
-        for (int v = 0; v < 2; v++) {  // psi, then lam: one register buffer live at a time
-            TileRegs<R> bb;
-            tile_load<R>(bb, (v == 0 ? psi : lam) + I.off, G, t);
-            T2 *dst = v == 0 ? tp : tl;
+        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
+        if (int(gt - t) != table_inst) {  // new instance: its RZ phase tables
+            __syncthreads();
+            build_phase_tables<R>(ph0, ph1, G, lr);
+            table_inst = int(gt - t);
+            __syncthreads();
+        }
+        {
+            // psi and lam of the thread's share (local l = threadIdx.x + 256 i),
+            // both in flight together
+            TileRegs<R> bp, bl;
+            tile_load<R>(bp, psi + I.off, G, t);
+            tile_load<R>(bl, lam + I.off, G, t);
+            constexpr int IT = TileRegs<R>::IT;
+            // the group's RZ gates act last in the layer and commute: every
+            // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x)
+            // is taken from the same state, then the diagonal is un-applied.
+            // Rotated bits below 8 depend on the thread only, bits 8.. on i.
+            R wsum = 0, wreg[reg_bits<R>()];
 #pragma unroll
-            for (int i = 0; i < TileRegs<R>::IT; i++) {
+            for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] = 0;
+#pragma unroll
+            for (int i = 0; i < IT; i++) {
                 const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
                 if (l >= sz) continue;
-                T2 a = bb.v[i];
+                T2 a = bp.v[i], b = bl.v[i];
                 if (last && cz_ladder_odd(tile_global(G, t, l), I.n)) {  // undo the CZ ladder (self-inverse)
                     a.x = -a.x;
                     a.y = -a.y;
+                    b.x = -b.x;
+                    b.y = -b.y;
                 }
-                dst[sw(l)] = a;
-            }
-        }
-        const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
-        if (int(gt - t) != table_inst) {  // new instance: its RZ phase tables
-            build_phase_tables<R>(ph0, ph1, G, lr);
-            table_inst = int(gt - t);
-        }
-        __syncthreads();
-        // the group's RZ gates act last in the layer and commute: every
-        // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x) is taken
-        // from the same state, then the diagonal is un-applied from psi and lam
-        {
-            R gzr[T];
-#pragma unroll
-            for (int r = 0; r < T; r++) gzr[r] = 0;
-            for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-                const uint32_t o = sw(l);
-                T2 a = tp[o], b = tl[o];
                 const R w = b.x * a.y - b.y * a.x;
+                wsum += w;
 #pragma unroll
-                for (int r = 0; r < T; r++)
-                    if (r < G.nrot) gzr[r] += ((l >> (G.rb0 + r)) & 1) ? -w : w;
+                for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] += ((i >> rb) & 1) ? -w : w;
                 T2 ph = group_phase<R>(ph0, ph1, G, l);
                 ph.y = -ph.y;  // conjugate
-                tp[o] = cmul(ph, a);
-                tl[o] = cmul(ph, b);
+                bp.v[i] = cmul(ph, a);
+                bl.v[i] = cmul(ph, b);
             }
 #pragma unroll
             for (int r = 0; r < T; r++) {
                 if (r >= G.nrot) continue;
-                const double v = warp_sum(double(gzr[r]));
-                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[T + r], v);
+                const int lb = G.rb0 + r;
+                R v;
+                if (lb < 8) {
+                    v = ((threadIdx.x >> lb) & 1) ? -wsum : wsum;
+                } else {
+                    v = 0;
+#pragma unroll
+                    for (int rb = 0; rb < reg_bits<R>(); rb++)
+                        if (lb == 8 + rb) v = wreg[rb];
+                }
+                const double vs = warp_sum(double(v));
+                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[T + r], vs);
             }
+            // RY gradients and un-rotation of the register-held bits 8..
+#pragma unroll
+            for (int rb = 0; rb < reg_bits<R>(); rb++) {
+                const int lb = 8 + rb;
+                if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+                const Rot<R> r = lr[G.q0 + lb - G.rb0];
+                const int nact = int(sz >> 8);  // registers holding amplitudes (lb < T0, so >= 2)
+                R sy = 0;
+#pragma unroll
+                for (int i = 0; i < IT; i++)
+                    if (!((i >> rb) & 1) && i < nact)
+                        sy += adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r);
+                const double vs = warp_sum(double(sy));
+                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[lb - G.rb0], vs);
+            }
+            tile_put<R>(bp, tp, sz);
+            tile_put<R>(bl, tl, sz);
         }
         __syncthreads();
-        for (int r0 = 0; r0 < G.nrot; r0 += 3) {
-            const int nb = G.nrot - r0 < 3 ? G.nrot - r0 : 3;
-            int bits[3];
-            Rot<R> rr[3];
-            for (int i = 0; i < nb; i++) {
-                bits[i] = G.rb0 + r0 + i;
-                rr[i] = lr[G.q0 + r0 + i];
+        // RY gradients and un-rotation of the rotated bits below 8, through shared memory
+        {
+            const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
+            const Rot<R> *r = lr + G.q0;
+            auto flush_gy = [&](Acc<R> (&gy)[3], int r0, int nb) {
+                for (int i = 0; i < nb; i++) {
+                    const double vy = warp_sum(gy[i].value());
+                    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[r0 + i], vy);
+                }
+            };
+            if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
+                {
+                    Acc<R> gy[3];
+                    adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
+                    flush_gy(gy, 0, 3);
+                }
+                __syncthreads();
+                {
+                    Acc<R> gy[3];
+                    adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
+                    flush_gy(gy, 3, 3);
+                }
+                __syncthreads();
+                {
+                    Acc<R> gy[3];
+                    adj_round_ct<R, 6, 2>(tp, tl, G.T0, r + 6, gy);
+                    flush_gy(gy, 6, 2);
+                }
+                __syncthreads();
+            } else if (G.rb0 == 5 && hi == 8) {
+                Acc<R> gy[3];
+                adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
+                flush_gy(gy, 0, 3);
+                __syncthreads();
+            } else {
+                for (int b0 = G.rb0; b0 < hi; b0 += 3) {
+                    const int nb = hi - b0 < 3 ? hi - b0 : 3;
+                    int bits[3];
+                    Rot<R> rr[3];
+                    for (int i = 0; i < nb; i++) {
+                        bits[i] = b0 + i;
+                        rr[i] = lr[G.q0 + b0 - G.rb0 + i];
+                    }
+                    Acc<R> gy[3];
+                    if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
+                    else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
+                    else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                    flush_gy(gy, b0 - G.rb0, nb);
+                    __syncthreads();
+                }
             }
-            Acc<R> gy[3];
-            if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
-            else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
-            else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
-            for (int i = 0; i < nb; i++) {
-                const double vy = warp_sum(gy[i].value());
-                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[r0 + i], vy);
-            }
-            __syncthreads();
         }
         for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
             const uint64_t x = tile_global(G, t, l);

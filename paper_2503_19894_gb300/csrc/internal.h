@@ -136,6 +136,28 @@ constexpr size_t kMatSlotBytes = size_t(16) << 14;
 cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const void **dev);
 
 // Queue one prepared gate on sv's stream.
+// Staging geometry of a warp's "cube": 32 consecutive slices (rows) x the
+// members spanned by the first mb = min(k, 4) targets (mb member bits), i.e.
+// 5 + mb index bits: the 5 lowest non-target bits and q0..q_{mb-1}.  Address
+// bits 0..4 always belong to it, so the cube is made of runs of at least 32
+// contiguous amplitudes and a warp moves it with coalesced 16-byte chunks.
+// In shared memory cube element c sits in slot c ^ X(c >> 4): X maps the row
+// bits that land above bit 3 onto free slot bits 1..3, so 16-byte chunk
+// accesses (8 lanes per phase) never conflict and 8-byte row accesses
+// (16 lanes per phase) conflict at most 2-way (only when qubit 0 is a
+// target).  Offsets and slots are additive over disjoint bit fields: an
+// element is addressed by one per-lane entry combined with one per-round or
+// per-member entry.  Built on the host per gate (csrc/cube.cpp).
+struct CubeTables {
+    uint64_t g_lane[32];  // global offset (amplitudes) of cube element 2 * lane, from the cube base
+    uint64_t g_j[8];      // offset of element 64 * j (chunk round j; 2^(mb-1) rounds)
+    uint16_t s_lane[32];  // slot of element 2 * lane
+    uint16_t s_j[8];      // slot of element 64 * j
+    uint16_t s_row[32];   // slot of (row r = lane, member 0)
+    uint16_t s_mem[16];   // slot of (row 0, member m), m < 2^mb
+};
+CubeTables make_cube_tables(const int *q, int k);
+
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);

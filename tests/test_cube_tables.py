@@ -1,0 +1,29 @@
+"""The warp-cube staging tables (csrc/cube.cpp) checked on the host: the C++
+check in tests/native/ is compiled against the library's own host source and
+verifies the mapping, the bounds and the bank-conflict bounds for 30000 random
+gates (see the check's header)."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2503_19894_gb300", "csrc")
+
+
+def test_cube_tables(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path / "cube_check")
+    cmd = [gxx, "-O2", "-std=c++17", "-I", CSRC, "-I", "/usr/local/cuda/include",
+           os.path.join(ROOT, "tests", "native", "cube_tables_check.cpp"), os.path.join(CSRC, "cube.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    fields = dict(kv.rsplit("=", 1) for kv in out.stdout.split())
+    assert fields["bad"] == "0"
+    assert fields["worst_row(q0!=0)"] == "1"
+    assert int(fields["worst_row(q0==0)"]) <= 2
+    assert fields["worst_chunk"] == "1"
