@@ -489,14 +489,26 @@ def main():
         host[x] = 1
         hv = host.numpy()
 
+        parts = {"h2d": 0.0, "apply_calls": 0.0, "finish": 0.0}
+
         def e2e_step():
-            capi.cast_sv_copy_from_host(sv.handle, hv)
+            t0 = time.perf_counter()
+            capi.cast_sv_copy_from_host(sv.handle, hv)  # returns once the copy is done
+            t1 = time.perf_counter()
             capi.cast_apply_circuit(sv.handle, n, qft, None, opts)
             capi.cast_apply_circuit(sv.handle, n, rqc, None, opts)
-            return capi.cast_expectation(sv.handle, z0)
+            t2 = time.perf_counter()
+            z = capi.cast_expectation(sv.handle, z0)  # waits for the gates, reads the result
+            t3 = time.perf_counter()
+            parts["h2d"] += t1 - t0
+            parts["apply_calls"] += t2 - t1
+            parts["finish"] += t3 - t2
+            return z
 
         e2e_step()
         barrier()
+        for key in parts:
+            parts[key] = 0.0
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
@@ -506,7 +518,8 @@ def main():
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
         e2e = {"value": round(step_bytes * a.steps * world / float(et.item()) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": 8,
-               "ms_per_step": round(float(et.item()) / a.steps * 1e3, 2)}
+               "ms_per_step": round(float(et.item()) / a.steps * 1e3, 2),
+               "ms_per_step_parts": {k: round(v / a.steps * 1e3, 2) for k, v in parts.items()}}
         del host
     sv.close()
     capi.cast_plan_destroy(plan_q)

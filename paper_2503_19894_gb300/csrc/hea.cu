@@ -45,6 +45,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -134,47 +135,91 @@ __device__ __forceinline__ bool cz_ladder_odd(uint64_t x, int n) {
     return __popcll(x & (x >> 1) & m) & 1;
 }
 
-// XOR swizzle of the shared tile: bits 0..2 of the slot are flipped by bits
-// 3..5 of the index, so gathering 8 amplitudes that differ in index bits 0..2
-// (stride 8 across threads) spreads over the banks.  Bijective on any tile.
-__device__ __forceinline__ uint32_t sw(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+// XOR swizzle of the shared tile, linear over disjoint bits and bijective
+// on any tile; it only reads index bits 3..6, so sw(l + 256 i) = sw(l) + 256 i.
+// A shared-memory phase serves 32 banks = 16 complex64 or 8 complex128
+// amplitudes, so the lanes of a phase must land on distinct low slot bits
+// for every access pattern: consecutive indices (loads, stores), and the
+// register rounds on bits 0-2 (lanes vary index bits 3-6), 3-5 (lanes vary
+// bits 0-2 and 6), 6-7 and 5-7 (lanes vary bits 0-3).
+//   complex64:  bit 4 -> slot bit 0, bit 5 -> 1, bit 6 -> 2 and 3
+//   complex128: bits 3, 4, 5 -> slot bits 0, 1, 2
+template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
+template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) {
+    return l ^ ((l >> 4) & 3u) ^ (((l >> 6) & 1u) * 12u);
+}
+template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
 
-// Phase of the group's RZ gates for local index l: product over the rotated
-// qubits of (cz - i sz) (bit 0) or (cz + i sz) (bit 1), looked up from two
-// tables of up to 64 entries (rotated bits 0..5 and 6..11 of the group).
+// A thread's share of a tile: register i holds local index l = threadIdx.x +
+// 256 i, global index x0 + i * stride (the register index occupies global
+// bits s .. s + log2(IT) - 1, zero in x0) and shared slot sw<R>(threadIdx.x) + 256 i
+// (the swizzle only mixes bits 0..5).
+struct TileAddr {
+    uint64_t x0, stride;
+    int s;
+};
+__device__ __forceinline__ TileAddr tile_addr(const Geo &G, uint64_t t) {
+    TileAddr a;
+    a.x0 = tile_global(G, t, threadIdx.x);
+    a.s = G.contiguous ? 8 : G.p0 + 3;
+    a.stride = uint64_t(1) << a.s;
+    return a;
+}
+
+// CZ-ladder signs of a thread's registers (bit i set: odd number of adjacent
+// set pairs below bit n in x0 | (i << s)).  The pairs split into those of x0,
+// those inside i, and the two that straddle the register bits: (s-1, s) and
+// (s+w-1, s+w), w = number of register bits that hold amplitudes.
+__device__ __forceinline__ uint32_t cz_mask(const TileAddr &a, int w, int n) {
+    constexpr uint32_t kInner = 0xB848u;  // bit i: parity of popc(i & (i >> 1)), i < 16
+    const uint32_t c0 = cz_ladder_odd(a.x0, n) ? 0xFFFFu : 0u;
+    const uint32_t lo = a.s > 0 && ((a.x0 >> (a.s - 1)) & 1) ? 0xAAAAu : 0u;  // i bit 0 pairs with bit s-1
+    const uint32_t top = w == 1 ? 0xAAAAu : (w == 2 ? 0xCCCCu : (w == 3 ? 0xF0F0u : 0xFF00u));  // i bit w-1
+    const uint32_t hi = (w > 0 && ((a.x0 >> (a.s + w)) & 1)) ? top : 0u;
+    return c0 ^ kInner ^ lo ^ hi;
+}
+
+// Phase of the group's RZ gates, split by where the rotated local bits sit:
+// pa[l & 255] covers the bits below 8 (a thread's own), pb[i] the bits from 8
+// on (its register index); each entry is a product over those qubits of
+// (cz - i sz) for bit 0 or (cz + i sz) for bit 1.
 template <typename R>
-__device__ void build_phase_tables(typename Cx<R>::T *ph0, typename Cx<R>::T *ph1, const Geo &G,
-                                   const Rot<R> *rots) {
+__device__ void phase_factors(typename Cx<R>::T *pa, typename Cx<R>::T *pb, const Geo &G,
+                                  const Rot<R> *rots) {
     using T2 = typename Cx<R>::T;
-    const int n0 = G.nrot < 6 ? G.nrot : 6, n1 = G.nrot - n0;
-    for (int e = threadIdx.x; e < (1 << n0) + (1 << n1); e += blockDim.x) {
-        const bool first = e < (1 << n0);
-        const int idx = first ? e : e - (1 << n0);
-        const int nb = first ? n0 : n1, r0 = first ? 0 : 6;
+    for (int e = threadIdx.x; e < 256 + 16; e += blockDim.x) {
+        const bool low = e < 256;
+        const uint32_t idx = low ? uint32_t(e) : uint32_t(e - 256);
         R re = 1, im = 0;
-        for (int i = 0; i < nb; i++) {
-            const Rot<R> r = rots[G.q0 + r0 + i];
-            const R s = ((idx >> i) & 1) ? r.sz : -r.sz;  // cz + i s
-            const R nre = re * r.cz - im * s, nim = re * s + im * r.cz;
+        for (int r = 0; r < G.nrot; r++) {
+            const int lb = G.rb0 + r;
+            if (low != (lb < 8)) continue;
+            const Rot<R> q = rots[G.q0 + r];
+            const R sg = ((idx >> (low ? lb : lb - 8)) & 1) ? q.sz : -q.sz;  // cz + i sg
+            const R nre = re * q.cz - im * sg, nim = re * sg + im * q.cz;
             re = nre;
             im = nim;
         }
         T2 v;
         v.x = re;
         v.y = im;
-        if (first) ph0[idx] = v;
-        else ph1[idx] = v;
+        if (low) pa[idx] = v;
+        else pb[idx] = v;
     }
 }
 
+// pa and pb, plus (groups whose rotated bits start at 5 or above, where pa
+// depends on the warp only) their products pc[warp * 16 + i]: the phase of a
+// register is then one broadcast load.  Ends with a barrier.
 template <typename R>
-__device__ __forceinline__ typename Cx<R>::T group_phase(const typename Cx<R>::T *ph0,
-                                                         const typename Cx<R>::T *ph1, const Geo &G, uint32_t l) {
-    const int n0 = G.nrot < 6 ? G.nrot : 6, n1 = G.nrot - n0;
-    const typename Cx<R>::T a = ph0[(l >> G.rb0) & ((1u << n0) - 1)];
-    if (n1 == 0) return a;
-    return cmul(a, ph1[(l >> (G.rb0 + 6)) & ((1u << n1) - 1)]);
+__device__ void build_split_phase(typename Cx<R>::T *pa, typename Cx<R>::T *pb, typename Cx<R>::T *pc, const Geo &G,
+                                  const Rot<R> *rots) {
+    phase_factors<R>(pa, pb, G, rots);
+    __syncthreads();
+    if (G.rb0 >= 5 && threadIdx.x < 128) pc[threadIdx.x] = cmul(pa[(threadIdx.x >> 4) << 5], pb[threadIdx.x & 15u]);
+    __syncthreads();
 }
+
 
 // locate the instance of global tile index gt (binary search on the prefix)
 __device__ __forceinline__ int find_inst(const PassArgs &P, uint64_t gt) {
@@ -224,7 +269,7 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            v[j] = tile[sw(o)];
+            v[j] = tile[sw<R>(o)];
         }
 #pragma unroll
         for (int i = 0; i < NB; i++)
@@ -237,23 +282,23 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            tile[sw(o)] = v[j];
+            tile[sw<R>(o)] = v[j];
         }
     }
 }
 
 // The same round with the NB rotated bits B0 .. B0+NB-1 fixed at compile
-// time.  The swizzle is linear over disjoint bits (sw(a | b) = sw(a) ^ sw(b)),
+// time.  The swizzle is linear over disjoint bits (sw<R>(a | b) = sw<R>(a) ^ sw<R>(b)),
 // so each member's slot is the sub-slice's slot XOR a constant.
 template <typename R, int B0, int NB>
 __device__ void tile_round_ct(typename Cx<R>::T *tile, int T0, const Rot<R> *rot) {
     using T2 = typename Cx<R>::T;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
-        const uint32_t sb = sw(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
+        const uint32_t sb = sw<R>(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
         T2 v[1 << NB];
 #pragma unroll
-        for (int j = 0; j < (1 << NB); j++) v[j] = tile[sb ^ sw(uint32_t(j) << B0)];
+        for (int j = 0; j < (1 << NB); j++) v[j] = tile[sb ^ sw<R>(uint32_t(j) << B0)];
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             const Rot<R> ri = rot[i];
@@ -262,7 +307,7 @@ __device__ void tile_round_ct(typename Cx<R>::T *tile, int T0, const Rot<R> *rot
                 if (!((j >> i) & 1)) fwd_pair(v[j], v[j | (1 << i)], ri);
         }
 #pragma unroll
-        for (int j = 0; j < (1 << NB); j++) tile[sb ^ sw(uint32_t(j) << B0)] = v[j];
+        for (int j = 0; j < (1 << NB); j++) tile[sb ^ sw<R>(uint32_t(j) << B0)] = v[j];
     }
 }
 
@@ -332,23 +377,19 @@ struct TileRegs {
 };
 
 template <typename R>
-__device__ __forceinline__ void tile_load(TileRegs<R> &b, const typename Cx<R>::T *__restrict__ sv, const Geo &G,
-                                          uint64_t t) {
-    const uint32_t sz = 1u << G.T0;
+__device__ __forceinline__ void tile_load(TileRegs<R> &b, const typename Cx<R>::T *__restrict__ sv, const TileAddr &a,
+                                          uint32_t sz) {
 #pragma unroll
-    for (int i = 0; i < TileRegs<R>::IT; i++) {
-        const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
-        if (l < sz) b.v[i] = sv[tile_global(G, t, l)];
-    }
+    for (int i = 0; i < TileRegs<R>::IT; i++)
+        if (threadIdx.x + uint32_t(i) * kThreads < sz) b.v[i] = sv[a.x0 + uint64_t(i) * a.stride];
 }
 
 template <typename R>
 __device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename Cx<R>::T *tile, uint32_t sz) {
+    const uint32_t s0 = sw<R>(threadIdx.x);
 #pragma unroll
-    for (int i = 0; i < TileRegs<R>::IT; i++) {
-        const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
-        if (l < sz) tile[sw(l)] = b.v[i];
-    }
+    for (int i = 0; i < TileRegs<R>::IT; i++)
+        if (threadIdx.x + uint32_t(i) * kThreads < sz) tile[s0 + uint32_t(i) * kThreads] = b.v[i];
 }
 
 template <typename R>
@@ -357,8 +398,9 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
               const Rot<R> *__restrict__ rot, const __grid_constant__ PassArgs P) {
     using T2 = typename Cx<R>::T;
     constexpr int T = tile_bits<R>();
+    constexpr int IT = TileRegs<R>::IT;
     __shared__ __align__(16) T2 tile[1 << T];
-    __shared__ __align__(16) T2 ph0[64], ph1[64];
+    __shared__ __align__(16) T2 pa[256], pb[16], pc[128];
     const uint64_t total = P.prefix[P.ninst];
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
@@ -371,7 +413,7 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
     HeaInst I = insts[P.inst[k]];
     Geo G = geometry(I.n, P.group, T);
     uint64_t t = t_begin - P.prefix[k];
-    tile_load<R>(buf, arena + I.off, G, t);
+    tile_load<R>(buf, arena + I.off, tile_addr(G, t), 1u << G.T0);
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
         const uint32_t sz = 1u << G.T0;
         const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
@@ -384,30 +426,42 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
         // instance starts at prefix = gt - tc); rebuilt when it changes
         const int inst_id = int(gt - tc);
         if (inst_id != table_inst) {
-            __syncthreads();  // the previous tile's stores read the old tables
-            build_phase_tables<R>(ph0, ph1, Gc, lr);
+            build_split_phase<R>(pa, pb, pc, Gc, lr);
             table_inst = inst_id;
+        } else {
+            __syncthreads();
         }
-        __syncthreads();
         if (gt + 1 < t_end) {
             k = find_inst(P, gt + 1);
             I = insts[P.inst[k]];
             G = geometry(I.n, P.group, T);
             t = gt + 1 - P.prefix[k];
-            tile_load<R>(buf, arena + I.off, G, t);
+            tile_load<R>(buf, arena + I.off, tile_addr(G, t), 1u << G.T0);
         }
         smem_rotations<R>(tile, Gc, lr);
-        const bool last = P.group == Ic.ngroups - 1;
+        // the group's RZ gates as one diagonal, then (last group) the CZ ladder
+        const TileAddr a = tile_addr(Gc, tc);
+        const uint32_t czm = (P.group == Ic.ngroups - 1)
+                                 ? cz_mask(a, Gc.T0 > 8 ? Gc.T0 - 8 : 0, Ic.n) : 0u;
+        const uint32_t s0 = sw<R>(threadIdx.x);
         T2 *sv = arena + Ic.off;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(Gc, tc, l);
-            T2 v = cmul(group_phase<R>(ph0, ph1, Gc, l), tile[sw(l)]);
-            if (last && cz_ladder_odd(x, Ic.n)) {
-                v.x = -v.x;
-                v.y = -v.y;
+        auto store = [&](auto warp_phase) {
+            const T2 pt = pa[threadIdx.x & 255u];
+            const T2 *pw = pc + ((threadIdx.x >> 5) << 4);
+#pragma unroll
+            for (int i = 0; i < IT; i++) {
+                if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
+                const T2 ph = warp_phase.value ? pw[i] : cmul(pt, pb[i]);
+                T2 v = cmul(ph, tile[s0 + uint32_t(i) * kThreads]);
+                if ((czm >> i) & 1) {
+                    v.x = -v.x;
+                    v.y = -v.y;
+                }
+                sv[a.x0 + uint64_t(i) * a.stride] = v;
             }
-            sv[x] = v;
-        }
+        };
+        if (Gc.rb0 >= 5) store(std::true_type{});
+        else store(std::false_type{});
         __syncthreads();
     }
 }
@@ -458,7 +512,8 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
         Acc<R> acc;
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
         TileRegs<R> buf;
-        tile_load<R>(buf, sv, G, t);
+        const TileAddr ta = tile_addr(G, t);
+        tile_load<R>(buf, sv, ta, sz);
         tile_put<R>(buf, tile, sz);
         if (P.group == 0) {
             const R zzr = R(zz);
@@ -466,7 +521,7 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
             for (int i = 0; i < TileRegs<R>::IT; i++) {
                 const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
                 if (l >= sz) continue;
-                const uint64_t x = tile_global(G, t, l);
+                const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
                 const T2 v = buf.v[i];
                 acc.add(zzr * R(I.n - 1 - 2 * odd) * (v.x * v.x + v.y * v.y));
@@ -478,7 +533,7 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
             const int b = G.rb0 + r;
             for (uint32_t p = threadIdx.x; p < (sz >> 1); p += blockDim.x) {
                 const uint32_t l0 = ((p >> b) << (b + 1)) | (p & ((1u << b) - 1));
-                const T2 a = tile[sw(l0)], c = tile[sw(l0 | (1u << b))];
+                const T2 a = tile[sw<R>(l0)], c = tile[sw<R>(l0 | (1u << b))];
                 acc.add(R(2.0 * hx) * (a.x * c.x + a.y * c.y));
             }
         }
@@ -508,28 +563,29 @@ k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__res
         const Geo G = geometry(I.n, P.group, T);
         const uint64_t t = gt - P.prefix[k];
         const uint32_t sz = 1u << G.T0;
+        const TileAddr ta = tile_addr(G, t);
         {
             TileRegs<R> buf;
-            tile_load<R>(buf, psi + I.off, G, t);
+            tile_load<R>(buf, psi + I.off, ta, sz);
             tile_put<R>(buf, tile, sz);
         }
         __syncthreads();
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(G, t, l);
+        for (uint32_t l = threadIdx.x, i = 0; l < sz; l += blockDim.x, i++) {
+            const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
             T2 out;
             out.x = 0;
             out.y = 0;
             if (P.group == 0) {
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
                 const R d = R(zz * double(I.n - 1 - 2 * odd));
-                out.x = d * tile[sw(l)].x;
-                out.y = d * tile[sw(l)].y;
+                out.x = d * tile[sw<R>(l)].x;
+                out.y = d * tile[sw<R>(l)].y;
             } else {
                 out = lam[I.off + x];
             }
             for (int r = 0; r < G.nrot; r++) {
-                const T2 nb = tile[sw(l ^ (1u << (G.rb0 + r)))];
+                const T2 nb = tile[sw<R>(l ^ (1u << (G.rb0 + r)))];
                 out.x += R(hx) * nb.x;
                 out.y += R(hx) * nb.y;
             }
@@ -560,8 +616,8 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            p[j] = tp[sw(o)];
-            l[j] = tl[sw(o)];
+            p[j] = tp[sw<R>(o)];
+            l[j] = tl[sw<R>(o)];
         }
 #pragma unroll
         for (int i = 0; i < NB; i++) {
@@ -586,8 +642,8 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
             for (int i = 0; i < NB; i++)
                 if ((j >> i) & 1) o |= 1u << bits[i];
-            tp[sw(o)] = p[j];
-            tl[sw(o)] = l[j];
+            tp[sw<R>(o)] = p[j];
+            tl[sw<R>(o)] = l[j];
         }
     }
 }
@@ -610,12 +666,12 @@ __device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T
     using T2 = typename Cx<R>::T;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
-        const uint32_t sb = sw(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
+        const uint32_t sb = sw<R>(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
         T2 p[1 << NB], l[1 << NB];
 #pragma unroll
         for (int j = 0; j < (1 << NB); j++) {
-            p[j] = tp[sb ^ sw(uint32_t(j) << B0)];
-            l[j] = tl[sb ^ sw(uint32_t(j) << B0)];
+            p[j] = tp[sb ^ sw<R>(uint32_t(j) << B0)];
+            l[j] = tl[sb ^ sw<R>(uint32_t(j) << B0)];
         }
 #pragma unroll
         for (int i = 0; i < NB; i++) {
@@ -628,10 +684,18 @@ __device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T
         }
 #pragma unroll
         for (int j = 0; j < (1 << NB); j++) {
-            tp[sb ^ sw(uint32_t(j) << B0)] = p[j];
-            tl[sb ^ sw(uint32_t(j) << B0)] = l[j];
+            tp[sb ^ sw<R>(uint32_t(j) << B0)] = p[j];
+            tl[sb ^ sw<R>(uint32_t(j) << B0)] = l[j];
         }
     }
+}
+
+// warp sum in the arithmetic type of the state (fp32 for complex64)
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 template <typename R>
@@ -641,30 +705,43 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                const __grid_constant__ PassArgs P, double *__restrict__ grad) {
     using T2 = typename Cx<R>::T;
     constexpr int T = tile_bits<R>();
+    constexpr int IT = TileRegs<R>::IT;
+    constexpr int NW = kThreads / 32;
     extern __shared__ __align__(16) unsigned char hea_smem[];  // psi tile, lam tile (64 KB)
     T2 *tp = reinterpret_cast<T2 *>(hea_smem);
     T2 *tl = tp + (1 << T);
-    __shared__ double gacc[2 * T];  // [RY of each rotated qubit][RZ of each]
-    __shared__ __align__(16) T2 ph0[64], ph1[64];
+    // per-warp gradient sums, [warp][RY of each rotated qubit, RZ of each]:
+    // each warp's lane 0 adds its per-tile sums, no atomics; summed over the
+    // warps and sent to global memory when the instance changes
+    __shared__ double gacc[NW][2 * T];
+    __shared__ __align__(16) T2 pa[256], pb[16], pc[128];
     int table_inst = -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t total = P.prefix[P.ninst];
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
-    for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) gacc[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * 2 * T; i += blockDim.x) (&gacc[0][0])[i] = 0.0;
     int cur = -1, cur_n = 0, cur_q0 = 0, cur_nrot = 0;
     int cur_poff = 0;
     auto flush = [&]() {
-        // gacc[r] -> RY of qubit q0 + r, gacc[T + r] -> RZ of qubit q0 + r
+        // gacc[.][r] -> RY of qubit q0 + r, gacc[.][T + r] -> RZ of qubit q0 + r
         for (int i = threadIdx.x; i < 2 * T; i += blockDim.x) {
             const int r = i % T;
-            if (r < cur_nrot && gacc[i] != 0.0) {
+            double v = 0.0;
+            for (int w = 0; w < NW; w++) {
+                v += gacc[w][i];
+                gacc[w][i] = 0.0;
+            }
+            if (r < cur_nrot && v != 0.0) {
                 const int q = cur_q0 + r;
                 const int p = cur_poff + 2 * cur_n * P.layer + (i < T ? q : cur_n + q);
-                atomicAdd(grad + p, gacc[i]);
+                atomicAdd(grad + p, v);
             }
-            gacc[i] = 0.0;
         }
+    };
+    auto add = [&](int slot, R v) {  // lane 0 holds the warp's sum
+        if (lane == 0) gacc[warp][slot] += double(v);
     };
     __syncthreads();
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
@@ -688,17 +765,16 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
         const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
         if (int(gt - t) != table_inst) {  // new instance: its RZ phase tables
             __syncthreads();
-            build_phase_tables<R>(ph0, ph1, G, lr);
+            build_split_phase<R>(pa, pb, pc, G, lr);
             table_inst = int(gt - t);
-            __syncthreads();
         }
+        const TileAddr ta = tile_addr(G, t);
         {
-            // psi and lam of the thread's share (local l = threadIdx.x + 256 i),
-            // both in flight together
+            // psi and lam of the thread's share, both in flight together
             TileRegs<R> bp, bl;
-            tile_load<R>(bp, psi + I.off, G, t);
-            tile_load<R>(bl, lam + I.off, G, t);
-            constexpr int IT = TileRegs<R>::IT;
+            tile_load<R>(bp, psi + I.off, ta, sz);
+            tile_load<R>(bl, lam + I.off, ta, sz);
+            const uint32_t czm = last ? cz_mask(ta, G.T0 > 8 ? G.T0 - 8 : 0, I.n) : 0u;
             // the group's RZ gates act last in the layer and commute: every
             // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x)
             // is taken from the same state, then the diagonal is un-applied.
@@ -706,41 +782,60 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
             R wsum = 0, wreg[reg_bits<R>()];
 #pragma unroll
             for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] = 0;
+            auto rz = [&](auto warp_phase) {
+                const T2 pt = pa[threadIdx.x & 255u];
+                const T2 *pw = pc + ((threadIdx.x >> 5) << 4);
 #pragma unroll
-            for (int i = 0; i < IT; i++) {
-                const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
-                if (l >= sz) continue;
-                T2 a = bp.v[i], b = bl.v[i];
-                if (last && cz_ladder_odd(tile_global(G, t, l), I.n)) {  // undo the CZ ladder (self-inverse)
-                    a.x = -a.x;
-                    a.y = -a.y;
-                    b.x = -b.x;
-                    b.y = -b.y;
+                for (int i = 0; i < IT; i++) {
+                    if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
+                    T2 a = bp.v[i], b = bl.v[i];
+                    if ((czm >> i) & 1) {  // undo the CZ ladder (self-inverse)
+                        a.x = -a.x;
+                        a.y = -a.y;
+                        b.x = -b.x;
+                        b.y = -b.y;
+                    }
+                    const R w = b.x * a.y - b.y * a.x;
+                    wsum += w;
+#pragma unroll
+                    for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] += ((i >> rb) & 1) ? -w : w;
+                    T2 ph = warp_phase.value ? pw[i] : cmul(pt, pb[i]);
+                    ph.y = -ph.y;  // conjugate
+                    bp.v[i] = cmul(ph, a);
+                    bl.v[i] = cmul(ph, b);
                 }
-                const R w = b.x * a.y - b.y * a.x;
-                wsum += w;
+            };
+            if (G.rb0 >= 5) rz(std::true_type{});
+            else rz(std::false_type{});
+            // sums over the warp with lane-dependent signs (rotated bits 0..4):
+            // a Walsh-Hadamard butterfly leaves sum_l (-1)^popc(j & l) w_l in lane j
+            R h = wsum;
 #pragma unroll
-                for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] += ((i >> rb) & 1) ? -w : w;
-                T2 ph = group_phase<R>(ph0, ph1, G, l);
-                ph.y = -ph.y;  // conjugate
-                bp.v[i] = cmul(ph, a);
-                bl.v[i] = cmul(ph, b);
+            for (int b = 0; b < 5; b++) {
+                const R o = __shfl_xor_sync(0xffffffffu, h, 1 << b);
+                h = ((lane >> b) & 1) ? (o - h) : (h + o);
+            }
+            R hl[5];
+#pragma unroll
+            for (int b = 0; b < 5; b++) hl[b] = __shfl_sync(0xffffffffu, h, 1 << b);
+            const R htot = __shfl_sync(0xffffffffu, h, 0);
+            for (int r = 0; r < G.nrot; r++) {
+                const int lb = G.rb0 + r;
+                if (lb < 5) {
+                    R v = 0;
+#pragma unroll
+                    for (int b = 0; b < 5; b++)
+                        if (lb == b) v = hl[b];
+                    add(T + r, v);
+                } else if (lb < 8) {
+                    add(T + r, ((threadIdx.x >> lb) & 1) ? -htot : htot);
+                }
             }
 #pragma unroll
-            for (int r = 0; r < T; r++) {
-                if (r >= G.nrot) continue;
-                const int lb = G.rb0 + r;
-                R v;
-                if (lb < 8) {
-                    v = ((threadIdx.x >> lb) & 1) ? -wsum : wsum;
-                } else {
-                    v = 0;
-#pragma unroll
-                    for (int rb = 0; rb < reg_bits<R>(); rb++)
-                        if (lb == 8 + rb) v = wreg[rb];
-                }
-                const double vs = warp_sum(double(v));
-                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[T + r], vs);
+            for (int rb = 0; rb < reg_bits<R>(); rb++) {
+                const int lb = 8 + rb;
+                if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+                add(T + lb - G.rb0, warp_sum_r<R>(wreg[rb]));
             }
             // RY gradients and un-rotation of the register-held bits 8..
 #pragma unroll
@@ -754,8 +849,7 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                 for (int i = 0; i < IT; i++)
                     if (!((i >> rb) & 1) && i < nact)
                         sy += adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r);
-                const double vs = warp_sum(double(sy));
-                if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[lb - G.rb0], vs);
+                add(lb - G.rb0, warp_sum_r<R>(sy));
             }
             tile_put<R>(bp, tp, sz);
             tile_put<R>(bl, tl, sz);
@@ -766,10 +860,7 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
             const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
             const Rot<R> *r = lr + G.q0;
             auto flush_gy = [&](Acc<R> (&gy)[3], int r0, int nb) {
-                for (int i = 0; i < nb; i++) {
-                    const double vy = warp_sum(gy[i].value());
-                    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[r0 + i], vy);
-                }
+                for (int i = 0; i < nb; i++) add(r0 + i, warp_sum_r<R>(R(gy[i].value())));
             };
             if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
                 {
@@ -813,10 +904,15 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                 }
             }
         }
-        for (uint32_t l = threadIdx.x; l < sz; l += blockDim.x) {
-            const uint64_t x = tile_global(G, t, l);
-            psi[I.off + x] = tp[sw(l)];
-            lam[I.off + x] = tl[sw(l)];
+        {
+            const uint32_t s0 = sw<R>(threadIdx.x);
+#pragma unroll
+            for (int i = 0; i < IT; i++) {
+                if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
+                const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
+                psi[I.off + x] = tp[s0 + uint32_t(i) * kThreads];
+                lam[I.off + x] = tl[s0 + uint32_t(i) * kThreads];
+            }
         }
         __syncthreads();
     }
