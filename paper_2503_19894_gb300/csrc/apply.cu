@@ -92,64 +92,87 @@ k_dense(typename Cx<R>::T *__restrict__ sv, uint64_t nslices, Targets tg,
 }
 
 // --------------------------------------------- dense complex64, staged cube
+// A stage holds CPI = 16 / 2^K consecutive cubes (4 KB for every K), so that
+// small gates keep as many bytes in flight per warp as k = 4.
 template <int K>
-constexpr int cube_ctas_per_sm() { return K <= 2 ? 4 : (K == 3 ? 3 : 2); }
+constexpr int cube_per_stage() { return K < 4 ? (16 >> K) : 1; }
 
 template <int K>
-__global__ void __launch_bounds__(256, cube_ctas_per_sm<K>())
+__global__ void __launch_bounds__(256, 3)
 k_dense_cube(float2 *__restrict__ sv, uint64_t ncubes, Targets tg, const __grid_constant__ DenseMat<float, K> U,
              const __grid_constant__ CubeTables ct) {
-    constexpr int D = 1 << K, E = 32 * D, CH = D / 2, NS = 2;
+    constexpr int D = 1 << K, E = 32 * D, CH = D / 2, NS = 2, CPI = cube_per_stage<K>();
     extern __shared__ __align__(16) unsigned char cube_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *stages = reinterpret_cast<float2 *>(cube_smem) + warp * (NS * E);
+    float2 *stages = reinterpret_cast<float2 *>(cube_smem) + warp * (NS * CPI * E);
     const uint64_t g_lane = ct.g_lane[lane];
     const uint32_t s_lane = ct.s_lane[lane], s_row = ct.s_row[lane];
+    const uint64_t nsup = ncubes / CPI;  // stage-sized groups of consecutive cubes
     const uint64_t wstep = uint64_t(gridDim.x) * (blockDim.x >> 5);
     auto cube_base = [&](uint64_t c) { return slice_base<K>(c * 32, tg) + g_lane; };
-    auto copy_async = [&](uint64_t c, float2 *stage) {
-        const float2 *b = sv + cube_base(c);
-        const uint32_t d = uint32_t(__cvta_generic_to_shared(stage));
+    auto copy_async = [&](uint64_t sc, float2 *stage) {
 #pragma unroll
-        for (int j = 0; j < CH; j++)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ ct.s_j[j]) >> 1) * 16u),
-                         "l"(b + ct.g_j[j])
-                         : "memory");
+        for (int u = 0; u < CPI; u++) {
+            const float2 *b = sv + cube_base(sc * CPI + u);
+            const uint32_t d = uint32_t(__cvta_generic_to_shared(stage + u * E));
+#pragma unroll
+            for (int j = 0; j < CH; j++)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ ct.s_j[j]) >> 1) * 16u),
+                             "l"(b + ct.g_j[j])
+                             : "memory");
+        }
     };
-    uint64_t c = uint64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
+    uint64_t sc = uint64_t(blockIdx.x) * (blockDim.x >> 5) + warp;
 #pragma unroll
     for (int si = 0; si < NS; si++) {
-        if (c + si * wstep < ncubes) copy_async(c + si * wstep, stages + si * E);
+        if (sc + si * wstep < nsup) copy_async(sc + si * wstep, stages + si * CPI * E);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    for (int si = 0; c < ncubes; c += wstep, si ^= 1) {
-        float2 *stage = stages + si * E;
+    for (int si = 0; sc < nsup; sc += wstep, si ^= 1) {
+        float2 *stage = stages + si * CPI * E;
         asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
         __syncwarp();
-        float2 x[D];
+#pragma unroll 1
+        for (int u = 0; u < CPI; u++) {
+            float2 *cube = stage + u * E;
+            float2 x[D];
+            if (K >= 2 && ct.pair) {  // members 2m, 2m+1 in one 16-byte chunk
 #pragma unroll
-        for (int m = 0; m < D; m++) x[m] = stage[s_row ^ ct.s_mem[m]];
-        // the row's slots belong to this lane alone: the outputs go in place
+                for (int m = 0; m < D; m += 2) {
+                    const float4 v = reinterpret_cast<const float4 *>(cube)[(s_row ^ ct.s_mem[m]) >> 1];
+                    x[m] = make_float2(v.x, v.y);
+                    x[m + 1] = make_float2(v.z, v.w);
+                }
+            } else {
 #pragma unroll
-        for (int r = 0; r < D; r++) {
-            float re = 0.f, im = 0.f;
-#pragma unroll
-            for (int cc = 0; cc < D; cc++) {
-                const float2 u = U.m[r][cc];
-                re = fmaf(u.x, x[cc].x, re);
-                re = fmaf(-u.y, x[cc].y, re);
-                im = fmaf(u.x, x[cc].y, im);
-                im = fmaf(u.y, x[cc].x, im);
+                for (int m = 0; m < D; m++) x[m] = cube[s_row ^ ct.s_mem[m]];
             }
-            stage[s_row ^ ct.s_mem[r]] = make_float2(re, im);
+            // the row's slots belong to this lane alone: the outputs go in place
+#pragma unroll
+            for (int r = 0; r < D; r++) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < D; cc++) {
+                    const float2 uu = U.m[r][cc];
+                    re = fmaf(uu.x, x[cc].x, re);
+                    re = fmaf(-uu.y, x[cc].y, re);
+                    im = fmaf(uu.x, x[cc].y, im);
+                    im = fmaf(uu.y, x[cc].x, im);
+                }
+                cube[s_row ^ ct.s_mem[r]] = make_float2(re, im);
+            }
         }
         __syncwarp();
-        float2 *b = sv + cube_base(c);
-        const float4 *s4 = reinterpret_cast<const float4 *>(stage);
 #pragma unroll
-        for (int j = 0; j < CH; j++) __stcs(reinterpret_cast<float4 *>(b + ct.g_j[j]), s4[(s_lane ^ ct.s_j[j]) >> 1]);
+        for (int u = 0; u < CPI; u++) {
+            float2 *b = sv + cube_base(sc * CPI + u);
+            const float4 *s4 = reinterpret_cast<const float4 *>(stage + u * E);
+#pragma unroll
+            for (int j = 0; j < CH; j++)
+                __stcs(reinterpret_cast<float4 *>(b + ct.g_j[j]), s4[(s_lane ^ ct.s_j[j]) >> 1]);
+        }
         __syncwarp();
-        if (c + NS * wstep < ncubes) copy_async(c + NS * wstep, stage);
+        if (sc + NS * wstep < nsup) copy_async(sc + NS * wstep, stage);
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -324,16 +347,17 @@ cast_status run_dense(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
         // cube is faster; otherwise the direct kernel is already coalesced.
         int L = 0;
         for (int i = 0; i < K; i++) L += (g.q[i] - i) < 5;
-        if (L >= 2 && sv->n >= K + 5) {  // staged cubes of 32 slices
+        constexpr int CPI = cube_per_stage<K>();
+        if (L >= 2 && sv->n >= K + 5 + (CPI == 16 ? 4 : CPI == 8 ? 3 : CPI == 4 ? 2 : CPI == 2 ? 1 : 0)) {
             DenseMat<float, K> U;
             for (int r = 0; r < (1 << K); r++)
                 for (int c = 0; c < (1 << K); c++) U.m[r][c] = to_dev<float>(g.m[size_t(r) * (1 << K) + c]);
             const CubeTables ct = make_cube_tables(g.q, K);
             const uint64_t ncubes = ns >> 5;
-            const size_t smem = size_t(8) * 2 * 32 * (1 << K) * sizeof(float2);
+            const size_t smem = size_t(8) * 2 * CPI * 32 * (1 << K) * sizeof(float2);  // 64 KB
             CAST_CUDA(cudaFuncSetAttribute(k_dense_cube<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            const int per_sm = tuned_blocks_per_sm(sv->dt, K, CLS_DENSE, cube_ctas_per_sm<K>());
-            const uint64_t want = (ncubes + 7) / 8, cap = uint64_t(sm_count_cached()) * per_sm;
+            const int per_sm = tuned_blocks_per_sm(sv->dt, K, CLS_DENSE, 3);
+            const uint64_t want = (ncubes / CPI + 7) / 8, cap = uint64_t(sm_count_cached()) * per_sm;
             ProfScope ps(sv->stream, "dense_k" + std::to_string(K) + "_" + dt_name(sv->dt),
                          2.0 * double(sizeof(T2)) * double(ns << K), 8.0 * double(ns << (2 * K)));
             k_dense_cube<K><<<(unsigned)(want < cap ? want : cap), 256, smem, sv->stream>>>(

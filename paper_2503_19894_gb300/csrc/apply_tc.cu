@@ -241,10 +241,18 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         for (int h = 0; h < 2; h++) {
             float v[MPT];
             tc::tmem_ld<MPT>(lane_addr + acc_col + 2 * j0 + MPT * h, v);
+            if (st.pair) {
 #pragma unroll
-            for (int m = 0; m < MPT / 2; m++)
-                stage[s_row ^ st.s_mem[h * (MPT / 2) + m]] =
-                    make_float2(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1]));
+                for (int m = 0; m < MPT / 2; m += 2)
+                    reinterpret_cast<float4 *>(stage)[(s_row ^ st.s_mem[h * (MPT / 2) + m]) >> 1] =
+                        make_float4(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1]),
+                                    fmaf(v[2 * m + 2], delta, v[2 * m + 2]), fmaf(v[2 * m + 3], delta, v[2 * m + 3]));
+            } else {
+#pragma unroll
+                for (int m = 0; m < MPT / 2; m++)
+                    stage[s_row ^ st.s_mem[h * (MPT / 2) + m]] =
+                        make_float2(fmaf(v[2 * m], delta, v[2 * m]), fmaf(v[2 * m + 1], delta, v[2 * m + 1]));
+            }
         }
         __syncwarp();
         float2 *b = sv + cube_base(t);
@@ -287,8 +295,17 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             float2 x[MPT / 2];
+            if (st.pair) {  // members 2m, 2m+1 in one 16-byte chunk
 #pragma unroll
-            for (int m = 0; m < MPT / 2; m++) x[m] = stage[s_row ^ st.s_mem[h * (MPT / 2) + m]];
+                for (int m = 0; m < MPT / 2; m += 2) {
+                    const float4 c = reinterpret_cast<const float4 *>(stage)[(s_row ^ st.s_mem[h * (MPT / 2) + m]) >> 1];
+                    x[m] = make_float2(c.x, c.y);
+                    x[m + 1] = make_float2(c.z, c.w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MPT / 2; m++) x[m] = stage[s_row ^ st.s_mem[h * (MPT / 2) + m]];
+            }
             float v[MPT];
 #pragma unroll
             for (int m = 0; m < MPT / 2; m++) {

@@ -73,6 +73,7 @@ CubeTables make_cube_tables(const int *q, int k) {
         ct.s_j[j] = j < rounds ? slot(64u * j) : 0;
     }
     for (int m = 0; m < 16; m++) ct.s_mem[m] = m < (1 << mb) ? slot(deposit(uint32_t(m), mpos, mb)) : 0;
+    ct.pair = (k >= 1 && q[0] == 0) ? 1u : 0u;
     return ct;
 }
 

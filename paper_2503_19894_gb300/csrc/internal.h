@@ -145,7 +145,7 @@ cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const voi
 // bits that land above bit 3 onto free slot bits 1..3, so 16-byte chunk
 // accesses (8 lanes per phase) never conflict and 8-byte row accesses
 // (16 lanes per phase) conflict at most 2-way (only when qubit 0 is a
-// target).  Offsets and slots are additive over disjoint bit fields: an
+// target; then 16-byte row accesses of member pairs are conflict-free).  Offsets and slots are additive over disjoint bit fields: an
 // element is addressed by one per-lane entry combined with one per-round or
 // per-member entry.  Built on the host per gate (csrc/cube.cpp).
 struct CubeTables {
@@ -155,6 +155,8 @@ struct CubeTables {
     uint16_t s_j[8];      // slot of element 64 * j
     uint16_t s_row[32];   // slot of (row r = lane, member 0)
     uint16_t s_mem[16];   // slot of (row 0, member m), m < 2^mb
+    uint32_t pair;        // q0 == 0: members 2m and 2m+1 of a row share one 16-byte chunk,
+                          // so rows move as 16-byte pairs (conflict-free, half the accesses)
 };
 CubeTables make_cube_tables(const int *q, int k);
 

@@ -5,7 +5,8 @@
 // by zero insertion, Eq. 4), all addresses lie inside the state, the chunk
 // accesses of each 8-lane phase hit 8 different 16-byte bank groups and the
 // row accesses of each half-warp at most 2-way share a bank pair (2-way only
-// when qubit 0 is a target).  Prints the counts; exit status 1 on a mismatch.
+// when qubit 0 is a target, whose rows then move as 16-byte member pairs
+// without conflicts).  Prints the counts; exit status 1 on a mismatch.
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -20,7 +21,7 @@ static uint64_t slice_base(uint64_t t, const int *q, int k) {
 }
 int main() {
     srand(11);
-    int bad = 0, worst_row = 0, worst_row_q0 = 0, worst_chunk = 0;
+    int bad = 0, worst_row = 0, worst_row_q0 = 0, worst_chunk = 0, worst_pair = 0;
     for (int trial = 0; trial < 30000; trial++) {
         int k = 1 + rand() % 6;
         int n = k + 7 + rand() % 20; if (n > 34) n = 34;
@@ -60,12 +61,25 @@ int main() {
             for (int r = 16 * hw; r < 16 * hw + 16; r++) { int bp = (ct.s_row[r] ^ ct.s_mem[m]) % 16; mx = std::max(mx, ++cnt[bp]); }
             if (q[0] == 0) worst_row_q0 = std::max(worst_row_q0, mx); else worst_row = std::max(worst_row, mx);
         }
+        // qubit 0 a target: member pairs (2m, 2m+1) share a 16-byte chunk, in
+        // order, and 16-byte row accesses (8 lanes per phase) do not conflict
+        if ((ct.pair != 0) != (q[0] == 0)) bad++;
+        if (ct.pair) {
+            for (int r = 0; r < 32; r++) if (ct.s_row[r] & 1) bad++;
+            for (int m = 0; m + 1 < M; m += 2) if (ct.s_mem[m + 1] != (ct.s_mem[m] ^ 1) || (ct.s_mem[m] & 1)) bad++;
+            for (int m = 0; m < M; m += 2) for (int p = 0; p < 4; p++) {
+                int cnt[8] = {0}, mx = 0;
+                for (int r = 8 * p; r < 8 * p + 8; r++) { int cp = ((ct.s_row[r] ^ ct.s_mem[m]) >> 1) % 8; mx = std::max(mx, ++cnt[cp]); }
+                worst_pair = std::max(worst_pair, mx);
+            }
+        }
         for (int j = 0; j < rounds; j++) for (int p = 0; p < 4; p++) {
             int cnt[8] = {0}, mx = 0;
             for (int lane = 8 * p; lane < 8 * p + 8; lane++) { int cp = ((ct.s_lane[lane] ^ ct.s_j[j]) >> 1) % 8; mx = std::max(mx, ++cnt[cp]); }
             worst_chunk = std::max(worst_chunk, mx);
         }
     }
-    printf("bad=%d worst_row(q0!=0)=%d worst_row(q0==0)=%d worst_chunk=%d\n", bad, worst_row, worst_row_q0, worst_chunk);
+    printf("bad=%d worst_row(q0!=0)=%d worst_row(q0==0)=%d worst_chunk=%d worst_pair=%d\n", bad, worst_row,
+           worst_row_q0, worst_chunk, worst_pair);
     return bad != 0;
 }

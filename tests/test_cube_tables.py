@@ -27,3 +27,4 @@ def test_cube_tables(tmp_path):
     assert fields["worst_row(q0!=0)"] == "1"
     assert int(fields["worst_row(q0==0)"]) <= 2
     assert fields["worst_chunk"] == "1"
+    assert fields["worst_pair"] == "1"
