@@ -440,7 +440,7 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     const uint64_t grid = ntiles < cap ? ntiles : cap;
     ProfScope ps(sv->stream, "tc_k" + std::to_string(K) + "_c64", 16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
-    const uint32_t inject = g_inject_limit.exchange(0);
+    const uint32_t inject = take_inject_limit();
     const CubeTables st = make_cube_tables(g.q, K);
     k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
                                                                inject ? inject : kWaitLimit, inject ? 1 : 0);
@@ -449,6 +449,10 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
 }
 
 }  // namespace
+
+bool tensor_mode_tf32x3() { return g_tensor_mode.load() == CAST_TC_TF32X3; }
+
+uint32_t take_inject_limit() { return g_inject_limit.exchange(0); }
 
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g) {
     return g_tensor_mode.load() == CAST_TC_TF32X3 && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary &&
@@ -465,6 +469,7 @@ cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g) {
 cast_status take_device_error() {
     int v = 0;
     CAST_CUDA(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)));
+    if (tc7_error_flag_take()) v = 1;
     if (v) {
         const int zero = 0;
         CAST_CUDA(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));

@@ -274,9 +274,9 @@ def tensor_mode():
     capi.cast_set_tensor_mode(old)
 
 
-@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("k", [4, 5, 6, 7])
 def test_tensor_core_gate_matches_oracle(k, tensor_mode):
-    """3xTF32 tcgen05 path (complex64, k = 4, 5, 6, n >= k + 7): every placement,
+    """3xTF32 tcgen05 path (complex64, k = 4..7, n >= k + 7): every placement,
     a single-tile state and multi-tile states with ragged CTA shares."""
     capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
     rng = np.random.default_rng(500 + k)
@@ -318,7 +318,7 @@ def test_tensor_core_fused_circuit(tensor_mode):
     sv.close()
 
 
-@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("k", [4, 5, 6, 7])
 def test_tensor_core_norm_does_not_drift(k, tensor_mode):
     """400 Haar k-qubit gates on the tensor cores: the per-slice norm
     restoration leaves unbiased noise, so the norm stays at 1 (a bias of the
