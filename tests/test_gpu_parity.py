@@ -90,6 +90,31 @@ def test_diag_with_unit_entries_and_identity(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_diag_partial_identity_all_placements(dtype, k):
+    """Diagonal gates with a random subset of identity entries: the kernel that
+    enumerates only the non-identity amplitudes (lowest target >= 2) and the
+    vector kernel (lowest target 0 or 1), small and multi-block states."""
+    rng = np.random.default_rng(700 + k)
+    for n in (k + 3, 12, 18):
+        psi0 = W.random_state(n, n)
+        for trial in range(4):
+            low = [0, 1, 2, 3][trial]  # lowest target
+            if low + k > n:
+                continue
+            rest = rng.choice(np.arange(low + 1, n), size=k - 1, replace=False) if k > 1 else []
+            qs = tuple(int(q) for q in rng.permutation([low] + list(rest)))
+            d = np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << k))
+            keep = rng.random(1 << k) < 0.5
+            keep[rng.integers(0, 1 << k)] = False  # at least one identity entry
+            keep[rng.integers(0, 1 << k)] = True   # at least one phase
+            d = np.where(keep, d, 1.0)
+            got = run_gate(n, dtype, psi0, qs, np.diag(d))
+            ref = oracle_gate(psi0, dtype, qs, np.diag(d))
+            assert np.max(np.abs(got - ref)) <= TOL[dtype], (n, qs)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_config0_random_circuit_unfused(dtype):
     """12-qubit random circuit, 20 layers, from |0...0>, no fusion: full state
     and <Z_0>."""
