@@ -469,7 +469,7 @@ cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g) {
 cast_status take_device_error() {
     int v = 0;
     CAST_CUDA(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)));
-    if (tc7_error_flag_take()) v = 1;
+    if (tcc_error_flag_take()) v = 1;
     if (v) {
         const int zero = 0;
         CAST_CUDA(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));

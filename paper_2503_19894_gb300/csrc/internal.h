@@ -164,9 +164,9 @@ cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
-bool tc7_eligible(const cast_sv *sv, const PreparedGate &g);  // dense k = 7 (apply_tc7.cu)
-cast_status launch_gate_tc7(cast_sv *sv, const PreparedGate &g);
-int tc7_error_flag_take();          // the k = 7 kernel's bounded-wait error flag, cleared
+bool tcc_eligible(const cast_sv *sv, const PreparedGate &g);  // dense k = 7, K-chunked (apply_tcc.cu)
+cast_status launch_gate_tcc(cast_sv *sv, const PreparedGate &g);
+int tcc_error_flag_take();          // the chunked kernel's bounded-wait error flag, cleared
 bool tensor_mode_tf32x3();          // cast_set_tensor_mode(CAST_TC_TF32X3) in effect
 uint32_t take_inject_limit();       // cast_debug_inject_timeout's pending limit, cleared (0: none)
 // Autotuned launch width (blocks per SM) of a CUDA-core kernel, or def.
