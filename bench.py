@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-vqa", action="store_true")
     p.add_argument("--no-c128", action="store_true")
+    p.add_argument("--ablation", action="store_true",
+                   help="add the fusion ablation: none / size-only / adaptive (operation counts) / adaptive "
+                        "(measured cost table, width search) on the same circuits")
     p.add_argument("--sweep", action="store_true",
                    help="add the dense-gate sweep (k = 1..7, low/high/mixed targets, every arithmetic mode)")
     return p.parse_args()
@@ -310,6 +313,46 @@ def sweep_bench(n, mp, reps=8):
             "tf32_peak_derived": round(tf32, 1), "results": out}
 
 
+def fusion_ablation(n, layers):
+    """Section IV's fusion modes on the benchmark circuits, on this GPU: fused
+    gate counts, host fusion time, device time per circuit pair and GB/s."""
+    import torch
+
+    import paper_2503_19894_gb300 as pkg
+    from paper_2503_19894_gb300 import capi
+    x, qft, rqc = workload(n, layers)
+    t0 = time.perf_counter()
+    table = capi.cast_autotune("c64", n)
+    tune_s = time.perf_counter() - t0
+    modes = (("none", capi.options("none", 5)), ("size_k5", capi.options("size", 5)),
+             ("adaptive_k5", capi.options("adaptive", 5)),
+             ("adaptive_measured_width_search", capi.options("adaptive", 0, cost=table)))
+    out = {}
+    sv = pkg.StateVector(n, "c64", init_index=x)
+    for name, opts in modes:
+        h0 = time.perf_counter()
+        plans = [capi.cast_plan_create(n, g, opts=opts, dtype="c64") for g in (qft, rqc)]
+        host_ms = (time.perf_counter() - h0) * 1e3
+        gates = [capi.cast_plan_info(p)[0] for p in plans]
+        for p in plans:  # warm-up
+            capi.cast_plan_apply(sv.handle, p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for p in plans:
+            capi.cast_plan_apply(sv.handle, p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"fused_gates": {"qft": gates[0], "rqc": gates[1]}, "device_ms": round(ms, 1),
+                     "host_fusion_ms": round(host_ms, 1),
+                     "gbs": round(sum(gates) * 2.0 * (1 << n) * 8 / (ms / 1e3) / 1e9, 1)}
+        for p in plans:
+            capi.cast_plan_destroy(p)
+    sv.close()
+    return {"n_qubits": n, "state": "complex64", "autotune_s": round(tune_s, 1), "modes": out}
+
+
 def vqa_bench():
     """Batched VQA (256 hardware-efficient-ansatz instances, n ~ U{16..24},
     10 layers, H = sum ZZ + 0.5 sum X) and 26-qubit adjoint gradients (20
@@ -545,6 +588,8 @@ def main():
             line["other_dtype"] = secondary_dtype(n, a.layers, a.max_k, "c128" if S == 8 else "c64")
         if world == 1 and not a.no_vqa:
             line["vqa"] = vqa_bench()
+        if world == 1 and a.ablation:
+            line["fusion_ablation"] = fusion_ablation(n, a.layers)
         if world == 1 and a.sweep:
             line["sweep"] = sweep_bench(n, mp)
         if world == 1 and not a.no_cpu:

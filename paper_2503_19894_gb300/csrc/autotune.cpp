@@ -76,6 +76,13 @@ cast_status cast_autotune(cast_dtype dt, int n, void *stream, cast_cost_table *o
     out->n_qubits = n;
     out->dtype = dt;
     const int ti = dt == CAST_C64 ? 0 : 1;
+    cast_cost_table saved_tab;
+    bool saved_have;
+    {  // the process-wide table is borrowed for the trial widths and restored below
+        std::lock_guard<std::mutex> lk(g_mu);
+        saved_tab = g_tab[ti];
+        saved_have = g_have[ti];
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -92,7 +99,7 @@ cast_status cast_autotune(cast_dtype dt, int n, void *stream, cast_cost_table *o
             for (int wi = 0; wi < 4 && st == CAST_OK; wi++) {
                 {  // try this width through the process-wide table
                     std::lock_guard<std::mutex> lk(g_mu);
-                    cast_cost_table t = g_have[ti] ? g_tab[ti] : *out;
+                    cast_cost_table t = *out;
                     t.dtype = dt;
                     t.blocks_per_sm[k][cls] = widths[wi];
                     g_tab[ti] = t;
@@ -119,7 +126,8 @@ cast_status cast_autotune(cast_dtype dt, int n, void *stream, cast_cost_table *o
     }
     {  // leave the process-wide table as it was before the call
         std::lock_guard<std::mutex> lk(g_mu);
-        g_have[ti] = false;
+        g_tab[ti] = saved_tab;
+        g_have[ti] = saved_have;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
