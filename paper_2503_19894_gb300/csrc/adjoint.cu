@@ -7,13 +7,15 @@
 // (x, x + 2^q) reads psi and lam, accumulates Im(conj(lam) . P psi) with an
 // FP64-class accumulator, and writes back U^dag psi and U^dag lam, where
 // U^dag = cos(theta/2) I + i sin(theta/2) P.  Each block leaves one partial
-// sum; they are reduced in a fixed order afterwards.
+// sum; they are reduced in a fixed order afterwards.  complex128 computes in
+// double-float arithmetic unless native FP64 is selected.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <string>
 
 #include "device.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace cast {
@@ -81,6 +83,76 @@ k_adj_rot(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ l
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
+// The same step for complex128 in double-float arithmetic on the FP32 pipe
+// (df64.cuh): the FP64 pipe of this part would make the step arithmetic-bound
+// at twice its memory time.  c, s arrive as (hi, lo) pairs.
+__device__ __forceinline__ void pauli_pair_df(int pauli, const df::CF &v0, const df::CF &v1, df::CF &o0, df::CF &o1) {
+    if (pauli == 1) {
+        o0 = v1;
+        o1 = v0;
+    } else if (pauli == 2) {  // Y|0> = i|1>, Y|1> = -i|0>
+        o0 = {v1.ih, v1.il, -v1.rh, -v1.rl};  // -i v1
+        o1 = {-v0.ih, -v0.il, v0.rh, v0.rl};  // i v0
+    } else {
+        o0 = v0;
+        o1 = {-v1.rh, -v1.rl, -v1.ih, -v1.il};
+    }
+}
+
+// U^dag v = c v + i s (P v)
+__device__ __forceinline__ double2 rot_df(const df::CF &v, const df::CF &pv, float ch, float cl, float sh, float sl) {
+    df::CF o = {0.f, 0.f, 0.f, 0.f};
+    df::mac(o.rh, o.rl, ch, cl, v.rh, v.rl);
+    df::msub(o.rh, o.rl, sh, sl, pv.ih, pv.il);
+    df::mac(o.ih, o.il, ch, cl, v.ih, v.il);
+    df::mac(o.ih, o.il, sh, sl, pv.rh, pv.rl);
+    return df::join_c(o);
+}
+
+__global__ void __launch_bounds__(256)
+k_adj_rot_df(double2 *__restrict__ psi, double2 *__restrict__ lam, uint64_t npairs, int q, int pauli, float ch,
+             float cl, float sh, float sl, double *__restrict__ partials) {
+    constexpr int UNR = 2;
+    float gh = 0.f, gl = 0.f;  // double-float sum of Im(conj(l) . P p)
+    const uint64_t bit = uint64_t(1) << q;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t t0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t0 < npairs; t0 += stride * UNR) {
+        double2 p0[UNR], p1[UNR], l0[UNR], l1[UNR];
+        uint64_t i0[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const uint64_t t = t0 + uint64_t(u) * stride;
+            i0[u] = ((t >> q) << (q + 1)) | (t & (bit - 1));
+            if (t < npairs) {
+                p0[u] = psi[i0[u]];
+                p1[u] = psi[i0[u] | bit];
+                l0[u] = lam[i0[u]];
+                l1[u] = lam[i0[u] | bit];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (t0 + uint64_t(u) * stride >= npairs) continue;
+            const df::CF a0 = df::split_c(p0[u]), a1 = df::split_c(p1[u]);
+            const df::CF b0 = df::split_c(l0[u]), b1 = df::split_c(l1[u]);
+            df::CF pa0, pa1, pb0, pb1;
+            pauli_pair_df(pauli, a0, a1, pa0, pa1);
+            pauli_pair_df(pauli, b0, b1, pb0, pb1);
+            // Im(conj(l) * pp) = l.re * pp.im - l.im * pp.re
+            df::mac(gh, gl, b0.rh, b0.rl, pa0.ih, pa0.il);
+            df::msub(gh, gl, b0.ih, b0.il, pa0.rh, pa0.rl);
+            df::mac(gh, gl, b1.rh, b1.rl, pa1.ih, pa1.il);
+            df::msub(gh, gl, b1.ih, b1.il, pa1.rh, pa1.rl);
+            psi[i0[u]] = rot_df(a0, pa0, ch, cl, sh, sl);
+            psi[i0[u] | bit] = rot_df(a1, pa1, ch, cl, sh, sl);
+            lam[i0[u]] = rot_df(b0, pb0, ch, cl, sh, sl);
+            lam[i0[u] | bit] = rot_df(b1, pb1, ch, cl, sh, sl);
+        }
+    }
+    const double v = block_sum(double(gh) + double(gl));
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
 // grad[p] = sum of the gate values whose parameter index is p, in gate order
 __global__ void k_param_sum(const double *__restrict__ gate_vals, const int *__restrict__ gate_pidx,
                             int ngates, double *__restrict__ grad, int nparams) {
@@ -105,7 +177,12 @@ cast_status launch_adjoint_rotation(cast_sv *psi, cast_sv *lam, int q, int pauli
         k_adj_rot<float><<<G, 256, 0, psi->stream>>>(reinterpret_cast<float2 *>(psi->data),
                                                       reinterpret_cast<float2 *>(lam->data), npairs, q,
                                                       pauli, (float)c, (float)s, d_partials);
-    else
+    else if (f64_mode() == CAST_F64_EMULATED) {
+        const float ch = float(c), cl = float(c - double(ch)), sh = float(s), sl = float(s - double(sh));
+        k_adj_rot_df<<<G, 256, 0, psi->stream>>>(reinterpret_cast<double2 *>(psi->data),
+                                                 reinterpret_cast<double2 *>(lam->data), npairs, q, pauli, ch, cl,
+                                                 sh, sl, d_partials);
+    } else
         k_adj_rot<double><<<G, 256, 0, psi->stream>>>(reinterpret_cast<double2 *>(psi->data),
                                                        reinterpret_cast<double2 *>(lam->data), npairs, q,
                                                        pauli, c, s, d_partials);

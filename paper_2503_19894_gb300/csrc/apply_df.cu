@@ -18,28 +18,10 @@ namespace {
 
 std::atomic<int> g_f64_mode{CAST_F64_EMULATED};
 
-struct CF {  // complex double-float: re = (rh, rl), im = (ih, il)
-    float rh, rl, ih, il;
-};
-
-__device__ __forceinline__ CF split_c(double2 v) {
-    const df::F2 a = df::split(v.x), b = df::split(v.y);
-    CF c;
-    c.rh = a.h; c.rl = a.l; c.ih = b.h; c.il = b.l;
-    return c;
-}
-
-// acc += u * x (complex, double-float)
-__device__ __forceinline__ void cmac(CF &acc, const CF &u, const CF &x) {
-    df::mac(acc.rh, acc.rl, u.rh, u.rl, x.rh, x.rl);
-    df::msub(acc.rh, acc.rl, u.ih, u.il, x.ih, x.il);
-    df::mac(acc.ih, acc.il, u.rh, u.rl, x.ih, x.il);
-    df::mac(acc.ih, acc.il, u.ih, u.il, x.rh, x.rl);
-}
-
-__device__ __forceinline__ double2 join_c(const CF &c) {
-    return make_double2(df::join(c.rh, c.rl), df::join(c.ih, c.il));
-}
+using df::CF;
+using df::cmac;
+using df::join_c;
+using df::split_c;
 
 CF host_split(cplx z) {
     CF c;

@@ -104,5 +104,30 @@ __device__ __forceinline__ void msub(float &sh, float &sl, float ah, float al, f
     mac(sh, sl, -ah, -al, bh, bl);
 }
 
+// complex double-float: re = (rh, rl), im = (ih, il)
+struct CF {
+    float rh, rl, ih, il;
+};
+
+__device__ __forceinline__ CF split_c(double2 v) {
+    const F2 a = split(v.x), b = split(v.y);
+    CF c;
+    c.rh = a.h;
+    c.rl = a.l;
+    c.ih = b.h;
+    c.il = b.l;
+    return c;
+}
+
+__device__ __forceinline__ double2 join_c(const CF &c) { return make_double2(join(c.rh, c.rl), join(c.ih, c.il)); }
+
+// acc += u * x (complex)
+__device__ __forceinline__ void cmac(CF &acc, const CF &u, const CF &x) {
+    mac(acc.rh, acc.rl, u.rh, u.rl, x.rh, x.rl);
+    msub(acc.rh, acc.rl, u.ih, u.il, x.ih, x.il);
+    mac(acc.ih, acc.il, u.rh, u.rl, x.ih, x.il);
+    mac(acc.ih, acc.il, u.ih, u.il, x.rh, x.rl);
+}
+
 }  // namespace df
 }  // namespace cast
