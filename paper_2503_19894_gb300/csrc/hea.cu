@@ -65,9 +65,180 @@ struct HeaInst {
     int rot_off;       // offset of its L x n rotation entries
 };
 
+// Arithmetic of a batch: complex64 (float), complex128 on the FP64 pipe
+// (double), or complex128-class double-float arithmetic on the FP32 pipe (DF:
+// a real is an unevaluated sum hi + lo of two floats, ~48 significant bits,
+// an amplitude (re_hi, re_lo, im_hi, im_lo)).  The batch's state arena is
+// private to it, so a DF batch keeps its amplitudes in that layout in HBM as
+// well (16 bytes, like complex128) and no FP64 conversion touches the
+// state; only the sums that leave a warp are formed in FP64.  Amp is the
+// amplitude type (HBM, registers and shared memory), Real a scalar.
+struct DF {};
+template <typename R> struct HT;
+template <> struct HT<float> {
+    using Amp = float2;
+    using Real = float;
+    static constexpr int T = 12;  // tile bits: 32 KB tiles
+};
+template <> struct HT<double> {
+    using Amp = double2;
+    using Real = double;
+    static constexpr int T = 11;
+};
+template <> struct HT<DF> {
+    using Amp = float4;
+    using Real = float2;
+    static constexpr int T = 11;
+};
+
 template <typename R>
 struct Rot {  // RY: [[c, -s], [s, c]];  RZ: diag(cz - i sz, cz + i sz)
-    R cy, sy, cz, sz;
+    typename HT<R>::Real cy, sy, cz, sz;
+};
+
+// ---- scalar and complex helpers per arithmetic
+__device__ __forceinline__ float rmul(float a, float b) { return a * b; }
+__device__ __forceinline__ double rmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 rmul(float2 a, float2 b) {  // double-float product
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float s = p + e;
+    return make_float2(s, e - (s - p));
+}
+__device__ __forceinline__ float radd(float a, float b) { return a + b; }
+__device__ __forceinline__ double radd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 radd(float2 a, float2 b) {  // double-float sum (TwoSum of the heads)
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float rneg(float a) { return -a; }
+__device__ __forceinline__ double rneg(double a) { return -a; }
+__device__ __forceinline__ float2 rneg(float2 a) { return make_float2(-a.x, -a.y); }
+// a b + c d
+__device__ __forceinline__ float rdot2(float a, float b, float c, float d) { return fmaf(a, b, c * d); }
+__device__ __forceinline__ double rdot2(double a, double b, double c, double d) { return fma(a, b, c * d); }
+__device__ __forceinline__ float2 rdot2(float2 a, float2 b, float2 c, float2 d) {
+    // exact head products (FMA error terms), TwoSum of the heads, the cross
+    // terms of the tails folded into the error, one renormalisation
+    const float p1 = a.x * b.x, p2 = c.x * d.x;
+    const float e1 = fmaf(a.x, b.x, -p1), e2 = fmaf(c.x, d.x, -p2);
+    const float s = p1 + p2;
+    const float bb = s - p1;
+    float t = (p1 - (s - bb)) + (p2 - bb);
+    t += e1 + e2;
+    t = fmaf(a.x, b.y, t);
+    t = fmaf(a.y, b.x, t);
+    t = fmaf(c.x, d.y, t);
+    t = fmaf(c.y, d.x, t);
+    const float h = s + t;
+    return make_float2(h, t - (h - s));
+}
+__device__ __forceinline__ double to_double(float a) { return double(a); }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(float2 a) { return double(a.x) + double(a.y); }
+// an integer (|v| < 2^24) as an exact Real
+template <typename Re> __device__ __forceinline__ Re rfrom_i(int v);
+template <> __device__ __forceinline__ float rfrom_i<float>(int v) { return float(v); }
+template <> __device__ __forceinline__ double rfrom_i<double>(int v) { return double(v); }
+template <> __device__ __forceinline__ float2 rfrom_i<float2>(int v) { return make_float2(float(v), 0.f); }
+// shuffles of a Real
+__device__ __forceinline__ float rshfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double rshfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ float2 rshfl_xor(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ __forceinline__ float rshfl(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ double rshfl(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float2 rshfl(float2 v, int l) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+}
+template <typename Re> __host__ __device__ __forceinline__ Re rfrom_d(double v);
+template <> __host__ __device__ __forceinline__ float rfrom_d<float>(double v) { return float(v); }
+template <> __host__ __device__ __forceinline__ double rfrom_d<double>(double v) { return v; }
+template <> __host__ __device__ __forceinline__ float2 rfrom_d<float2>(double v) {
+    const float h = float(v);
+    return make_float2(h, float(v - double(h)));
+}
+template <typename Re> __device__ __forceinline__ Re rzero();
+template <> __device__ __forceinline__ float rzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double rzero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float2 rzero<float2>() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ float re_of(float2 v) { return v.x; }
+__device__ __forceinline__ float im_of(float2 v) { return v.y; }
+__device__ __forceinline__ double re_of(double2 v) { return v.x; }
+__device__ __forceinline__ double im_of(double2 v) { return v.y; }
+__device__ __forceinline__ float2 re_of(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 im_of(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 make_amp(float re, float im) { return make_float2(re, im); }
+__device__ __forceinline__ double2 make_amp(double re, double im) { return make_double2(re, im); }
+__device__ __forceinline__ float4 make_amp(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+
+template <typename A>
+__device__ __forceinline__ A amul(A a, A b) {  // complex product
+    return make_amp(rdot2(re_of(a), re_of(b), rneg(im_of(a)), im_of(b)), rdot2(re_of(a), im_of(b), im_of(a), re_of(b)));
+}
+template <typename A>
+__device__ __forceinline__ A aneg(A a) {
+    return make_amp(rneg(re_of(a)), rneg(im_of(a)));
+}
+template <typename A>
+__device__ __forceinline__ A aconj(A a) {
+    return make_amp(re_of(a), rneg(im_of(a)));
+}
+template <typename A, typename Re>
+__device__ __forceinline__ A ascale(A a, Re r) {
+    return make_amp(rmul(re_of(a), r), rmul(im_of(a), r));
+}
+template <typename A>
+__device__ __forceinline__ A aadd(A a, A b) {
+    return make_amp(radd(re_of(a), re_of(b)), radd(im_of(a), im_of(b)));
+}
+// Im(conj(b) a) and Re(conj(a) c)
+template <typename A>
+__device__ __forceinline__ auto im_conj_mul(A b, A a) {
+    return rdot2(re_of(b), im_of(a), rneg(im_of(b)), re_of(a));
+}
+template <typename A>
+__device__ __forceinline__ auto re_conj_mul(A a, A c) {
+    return rdot2(re_of(a), re_of(c), im_of(a), im_of(c));
+}
+
+// warp sum of a Real in its own arithmetic (fp32 for complex64)
+template <typename Re>
+__device__ __forceinline__ Re warp_sum_r(Re v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = radd(v, rshfl_xor(v, o));
+    return v;
+}
+
+// A thread's running sum of Real values: compensated fp32 for complex64,
+// FP64 on the FP64 pipe, double-float for DF; get() returns it as a Real.
+template <typename R> struct RAcc;
+template <> struct RAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = hi + v;
+        const float bb = s - hi;
+        lo += (hi - (s - bb)) + (v - bb);
+        hi = s;
+    }
+    __device__ __forceinline__ float get() const { return hi + lo; }
+};
+template <> struct RAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct RAcc<DF> {
+    float2 s = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 v) { s = radd(s, v); }
+    __device__ __forceinline__ float2 get() const { return s; }
 };
 
 // one launch = (layer, group); instances with that group and their tile ranges
@@ -79,9 +250,7 @@ struct PassArgs {
     const uint64_t *prefix;  // tile prefix sums (ninst + 1)
 };
 
-template <typename R> constexpr int tile_bits();
-template <> constexpr int tile_bits<float>() { return 12; }
-template <> constexpr int tile_bits<double>() { return 11; }
+template <typename R> constexpr int tile_bits() { return HT<R>::T; }
 
 // Geometry of group g of an n-qubit instance for tile width T.
 struct Geo {
@@ -149,6 +318,7 @@ template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) {
     return l ^ ((l >> 4) & 3u) ^ (((l >> 6) & 1u) * 12u);
 }
 template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+template <> __device__ __forceinline__ uint32_t sw<DF>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
 
 // A thread's share of a tile: register i holds local index l = threadIdx.x +
 // 256 i, global index x0 + i * stride (the register index occupies global
@@ -184,25 +354,20 @@ __device__ __forceinline__ uint32_t cz_mask(const TileAddr &a, int w, int n) {
 // on (its register index); each entry is a product over those qubits of
 // (cz - i sz) for bit 0 or (cz + i sz) for bit 1.
 template <typename R>
-__device__ void phase_factors(typename Cx<R>::T *pa, typename Cx<R>::T *pb, const Geo &G,
-                                  const Rot<R> *rots) {
-    using T2 = typename Cx<R>::T;
+__device__ void phase_factors(typename HT<R>::Amp *pa, typename HT<R>::Amp *pb, const Geo &G, const Rot<R> *rots) {
+    using A = typename HT<R>::Amp;
+    using Re = typename HT<R>::Real;
     for (int e = threadIdx.x; e < 256 + 16; e += blockDim.x) {
         const bool low = e < 256;
         const uint32_t idx = low ? uint32_t(e) : uint32_t(e - 256);
-        R re = 1, im = 0;
+        A v = make_amp(rfrom_d<Re>(1.0), rzero<Re>());
         for (int r = 0; r < G.nrot; r++) {
             const int lb = G.rb0 + r;
             if (low != (lb < 8)) continue;
             const Rot<R> q = rots[G.q0 + r];
-            const R sg = ((idx >> (low ? lb : lb - 8)) & 1) ? q.sz : -q.sz;  // cz + i sg
-            const R nre = re * q.cz - im * sg, nim = re * sg + im * q.cz;
-            re = nre;
-            im = nim;
+            const Re sg = ((idx >> (low ? lb : lb - 8)) & 1) ? q.sz : rneg(q.sz);  // cz + i sg
+            v = amul(v, make_amp(q.cz, sg));
         }
-        T2 v;
-        v.x = re;
-        v.y = im;
         if (low) pa[idx] = v;
         else pb[idx] = v;
     }
@@ -212,11 +377,11 @@ __device__ void phase_factors(typename Cx<R>::T *pa, typename Cx<R>::T *pb, cons
 // depends on the warp only) their products pc[warp * 16 + i]: the phase of a
 // register is then one broadcast load.  Ends with a barrier.
 template <typename R>
-__device__ void build_split_phase(typename Cx<R>::T *pa, typename Cx<R>::T *pb, typename Cx<R>::T *pc, const Geo &G,
-                                  const Rot<R> *rots) {
+__device__ void build_split_phase(typename HT<R>::Amp *pa, typename HT<R>::Amp *pb, typename HT<R>::Amp *pc,
+                                  const Geo &G, const Rot<R> *rots) {
     phase_factors<R>(pa, pb, G, rots);
     __syncthreads();
-    if (G.rb0 >= 5 && threadIdx.x < 128) pc[threadIdx.x] = cmul(pa[(threadIdx.x >> 4) << 5], pb[threadIdx.x & 15u]);
+    if (G.rb0 >= 5 && threadIdx.x < 128) pc[threadIdx.x] = amul(pa[(threadIdx.x >> 4) << 5], pb[threadIdx.x & 15u]);
     __syncthreads();
 }
 
@@ -232,16 +397,13 @@ __device__ __forceinline__ int find_inst(const PassArgs &P, uint64_t gt) {
     return lo;
 }
 
-template <typename T2>
-__device__ __forceinline__ void ry(T2 &a, T2 &b, float c, float s) {
-    const T2 x = a, y = b;
-    a.x = c * x.x - s * y.x; a.y = c * x.y - s * y.y;
-    b.x = s * x.x + c * y.x; b.y = s * x.y + c * y.y;
-}
-__device__ __forceinline__ void ry(double2 &a, double2 &b, double c, double s) {
-    const double2 x = a, y = b;
-    a.x = c * x.x - s * y.x; a.y = c * x.y - s * y.y;
-    b.x = s * x.x + c * y.x; b.y = s * x.y + c * y.y;
+// (a, b) <- (c a - s b, s a + c b)
+template <typename A, typename Re>
+__device__ __forceinline__ void ry(A &a, A &b, Re c, Re s) {
+    const A x = a, y = b;
+    const Re ns = rneg(s);
+    a = make_amp(rdot2(c, re_of(x), ns, re_of(y)), rdot2(c, im_of(x), ns, im_of(y)));
+    b = make_amp(rdot2(s, re_of(x), c, re_of(y)), rdot2(s, im_of(x), c, im_of(y)));
 }
 // forward: RY_q on the pair (a, b) of qubit q (the group's RZ gates follow as
 // one diagonal phase when the tile is stored)
@@ -252,8 +414,8 @@ __device__ __forceinline__ void fwd_pair(T2 &a, T2 &b, const Rot<R> &r) {
 
 // apply the forward rotations of local bits bits[0..nb) (nb <= 3) to the tile
 template <typename R, int NB>
-__device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, const Rot<R> *rot) {
-    using T2 = typename Cx<R>::T;
+__device__ void tile_round(typename HT<R>::Amp *tile, int T0, const int *bits, const Rot<R> *rot) {
+    using T2 = typename HT<R>::Amp;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
         uint32_t base = s;
@@ -291,8 +453,8 @@ __device__ void tile_round(typename Cx<R>::T *tile, int T0, const int *bits, con
 // time.  The swizzle is linear over disjoint bits (sw<R>(a | b) = sw<R>(a) ^ sw<R>(b)),
 // so each member's slot is the sub-slice's slot XOR a constant.
 template <typename R, int B0, int NB>
-__device__ void tile_round_ct(typename Cx<R>::T *tile, int T0, const Rot<R> *rot) {
-    using T2 = typename Cx<R>::T;
+__device__ void tile_round_ct(typename HT<R>::Amp *tile, int T0, const Rot<R> *rot) {
+    using T2 = typename HT<R>::Amp;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
         const uint32_t sb = sw<R>(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
@@ -335,7 +497,7 @@ __device__ __forceinline__ void reg_rotations(Regs &b, const Geo &G, const Rot<R
 // registers): fixed rounds for the full-width groups, else rounds of three
 // with runtime bit positions.
 template <typename R>
-__device__ void smem_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot<R> *rots) {
+__device__ void smem_rotations(typename HT<R>::Amp *tile, const Geo &G, const Rot<R> *rots) {
     const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
     if (G.rb0 >= hi) return;
     const Rot<R> *r = rots + G.q0;  // RY/RZ entries of the group's rotated qubits, in order
@@ -373,19 +535,19 @@ __device__ void smem_rotations(typename Cx<R>::T *tile, const Geo &G, const Rot<
 template <typename R>
 struct TileRegs {
     static constexpr int IT = (1 << tile_bits<R>()) / kThreads;
-    typename Cx<R>::T v[IT];
+    typename HT<R>::Amp v[IT];
 };
 
 template <typename R>
-__device__ __forceinline__ void tile_load(TileRegs<R> &b, const typename Cx<R>::T *__restrict__ sv, const TileAddr &a,
+__device__ __forceinline__ void tile_load(TileRegs<R> &b, const typename HT<R>::Amp *__restrict__ sv, const TileAddr &a,
                                           uint32_t sz) {
 #pragma unroll
     for (int i = 0; i < TileRegs<R>::IT; i++)
-        if (threadIdx.x + uint32_t(i) * kThreads < sz) b.v[i] = sv[a.x0 + uint64_t(i) * a.stride];
+        if (threadIdx.x + uint32_t(i) * kThreads < sz) b.v[i] = (sv[a.x0 + uint64_t(i) * a.stride]);
 }
 
 template <typename R>
-__device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename Cx<R>::T *tile, uint32_t sz) {
+__device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename HT<R>::Amp *tile, uint32_t sz) {
     const uint32_t s0 = sw<R>(threadIdx.x);
 #pragma unroll
     for (int i = 0; i < TileRegs<R>::IT; i++)
@@ -394,9 +556,9 @@ __device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename Cx<R>::T
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
-k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts,
+k_hea_forward(typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict__ insts,
               const Rot<R> *__restrict__ rot, const __grid_constant__ PassArgs P) {
-    using T2 = typename Cx<R>::T;
+    using T2 = typename HT<R>::Amp;
     constexpr int T = tile_bits<R>();
     constexpr int IT = TileRegs<R>::IT;
     __shared__ __align__(16) T2 tile[1 << T];
@@ -444,20 +606,17 @@ k_hea_forward(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__
         const uint32_t czm = (P.group == Ic.ngroups - 1)
                                  ? cz_mask(a, Gc.T0 > 8 ? Gc.T0 - 8 : 0, Ic.n) : 0u;
         const uint32_t s0 = sw<R>(threadIdx.x);
-        T2 *sv = arena + Ic.off;
+        typename HT<R>::Amp *sv = arena + Ic.off;
         auto store = [&](auto warp_phase) {
             const T2 pt = pa[threadIdx.x & 255u];
             const T2 *pw = pc + ((threadIdx.x >> 5) << 4);
 #pragma unroll
             for (int i = 0; i < IT; i++) {
                 if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
-                const T2 ph = warp_phase.value ? pw[i] : cmul(pt, pb[i]);
-                T2 v = cmul(ph, tile[s0 + uint32_t(i) * kThreads]);
-                if ((czm >> i) & 1) {
-                    v.x = -v.x;
-                    v.y = -v.y;
-                }
-                sv[a.x0 + uint64_t(i) * a.stride] = v;
+                const T2 ph = warp_phase.value ? pw[i] : amul(pt, pb[i]);
+                T2 v = amul(ph, tile[s0 + uint32_t(i) * kThreads]);
+                if ((czm >> i) & 1) v = aneg(v);
+                sv[a.x0 + uint64_t(i) * a.stride] = (v);
             }
         };
         if (Gc.rb0 >= 5) store(std::true_type{});
@@ -483,9 +642,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // energy contribution of one group: ZZ (group 0 only) and X_q of the group's qubits
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts,
+k_hea_energy(const typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict__ insts,
              const __grid_constant__ PassArgs P, double zz, double hx, double *__restrict__ energy) {
-    using T2 = typename Cx<R>::T;
+    using T2 = typename HT<R>::Amp;
     constexpr int T = tile_bits<R>();
     __shared__ __align__(16) T2 tile[1 << T];
     __shared__ double slot;
@@ -507,16 +666,17 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
         const HeaInst I = insts[id];
         const Geo G = geometry(I.n, P.group, T);
         const uint64_t t = gt - P.prefix[k];
-        const T2 *sv = arena + I.off;
+        const typename HT<R>::Amp *sv = arena + I.off;
         const uint32_t sz = 1u << G.T0;
-        Acc<R> acc;
+        using Re = typename HT<R>::Real;
+        RAcc<R> acc;
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
         TileRegs<R> buf;
         const TileAddr ta = tile_addr(G, t);
         tile_load<R>(buf, sv, ta, sz);
         tile_put<R>(buf, tile, sz);
         if (P.group == 0) {
-            const R zzr = R(zz);
+            const Re zzr = rfrom_d<Re>(zz);
 #pragma unroll
             for (int i = 0; i < TileRegs<R>::IT; i++) {
                 const uint32_t l = threadIdx.x + uint32_t(i) * kThreads;
@@ -524,20 +684,21 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
                 const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
                 const T2 v = buf.v[i];
-                acc.add(zzr * R(I.n - 1 - 2 * odd) * (v.x * v.x + v.y * v.y));
+                acc.add(rmul(rmul(zzr, rfrom_i<Re>(I.n - 1 - 2 * odd)), re_conj_mul(v, v)));
             }
         }
         __syncthreads();
         // <X_q> = sum_x Re(conj(psi_x) psi_{x ^ 2^q}) = 2 sum_{x_q = 0} Re(...)
+        const Re hx2 = rfrom_d<Re>(2.0 * hx);
         for (int r = 0; r < G.nrot; r++) {
             const int b = G.rb0 + r;
             for (uint32_t p = threadIdx.x; p < (sz >> 1); p += blockDim.x) {
                 const uint32_t l0 = ((p >> b) << (b + 1)) | (p & ((1u << b) - 1));
                 const T2 a = tile[sw<R>(l0)], c = tile[sw<R>(l0 | (1u << b))];
-                acc.add(R(2.0 * hx) * (a.x * c.x + a.y * c.y));
+                acc.add(rmul(hx2, re_conj_mul(a, c)));
             }
         }
-        double v = warp_sum(acc.value());
+        const double v = to_double(warp_sum_r(acc.get()));
         if ((threadIdx.x & 31) == 0) atomicAdd(&slot, v);
         __syncthreads();
     }
@@ -548,9 +709,9 @@ k_hea_energy(const typename Cx<R>::T *__restrict__ arena, const HeaInst *__restr
 // lam = H psi for one group (group 0 writes, the others add)
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
+k_hea_lambda(const typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
              const HeaInst *__restrict__ insts, const __grid_constant__ PassArgs P, double zz, double hx) {
-    using T2 = typename Cx<R>::T;
+    using T2 = typename HT<R>::Amp;
     constexpr int T = tile_bits<R>();
     __shared__ __align__(16) T2 tile[1 << T];
     const uint64_t total = P.prefix[P.ninst];
@@ -571,36 +732,43 @@ k_hea_lambda(const typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__res
         }
         __syncthreads();
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
+        using Re = typename HT<R>::Real;
+        const Re zzr = rfrom_d<Re>(zz), hxr = rfrom_d<Re>(hx);
         for (uint32_t l = threadIdx.x, i = 0; l < sz; l += blockDim.x, i++) {
             const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
             T2 out;
-            out.x = 0;
-            out.y = 0;
             if (P.group == 0) {
                 const int odd = __popcll((x ^ (x >> 1)) & zmask);
-                const R d = R(zz * double(I.n - 1 - 2 * odd));
-                out.x = d * tile[sw<R>(l)].x;
-                out.y = d * tile[sw<R>(l)].y;
+                out = ascale(tile[sw<R>(l)], rmul(zzr, rfrom_i<Re>(I.n - 1 - 2 * odd)));
             } else {
-                out = lam[I.off + x];
+                out = (lam[I.off + x]);
             }
-            for (int r = 0; r < G.nrot; r++) {
-                const T2 nb = tile[sw<R>(l ^ (1u << (G.rb0 + r)))];
-                out.x += R(hx) * nb.x;
-                out.y += R(hx) * nb.y;
-            }
-            lam[I.off + x] = out;
+            for (int r = 0; r < G.nrot; r++) out = aadd(out, ascale(tile[sw<R>(l ^ (1u << (G.rb0 + r)))], hxr));
+            lam[I.off + x] = (out);
         }
         __syncthreads();
     }
 }
 
+// One RY_q pair of psi and lam in the backward sweep: the pair's share of
+// dE/dtheta_q = Im<lam|Y_q|psi> (Y psi = (-i p1, i p0):
+// Im(conj(l0)(-i p1)) = -Re(conj(l0) p1), Im(conj(l1)(i p0)) = Re(conj(l1) p0)),
+// then RY(-theta) on both.
+template <typename T2, typename R>
+__device__ __forceinline__ typename HT<R>::Real adj_pair(T2 &p0, T2 &p1, T2 &l0, T2 &l1, const Rot<R> &r) {
+    const auto g = radd(re_conj_mul(l1, p0), rneg(re_conj_mul(l0, p1)));
+    const auto ns = rneg(r.sy);
+    ry(p0, p1, r.cy, ns);
+    ry(l0, l1, r.cy, ns);
+    return g;
+}
+
 // backward sweep of one (layer, group) on psi and lam, with gradients: the RY
 // part of a round (the RZ gates were handled as one diagonal beforehand)
 template <typename R, int NB>
-__device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, const int *bits, const Rot<R> *rot,
-                          Acc<R> (&gy)[3]) {
-    using T2 = typename Cx<R>::T;
+__device__ void adj_round(typename HT<R>::Amp *tp, typename HT<R>::Amp *tl, int T0, const int *bits, const Rot<R> *rot,
+                          RAcc<R> (&gy)[3]) {
+    using T2 = typename HT<R>::Amp;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
         uint32_t base = s;
@@ -622,18 +790,10 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             const Rot<R> r = rot[i];
-            R sy = 0;  // this sub-slice's share, added to the compensated sum once
+            auto sy = rzero<typename HT<R>::Real>();  // this sub-slice's share, added to the sum once
 #pragma unroll
-            for (int j = 0; j < (1 << NB); j++) {
-                if ((j >> i) & 1) continue;
-                T2 &p0 = p[j], &p1 = p[j | (1 << i)], &l0 = l[j], &l1 = l[j | (1 << i)];
-                // dE/dtheta = Im<lam|Y|psi>; Y psi = (-i p1, i p0)
-                //   Im(conj(l0)(-i p1)) = -(l0.x p1.x + l0.y p1.y); Im(conj(l1)(i p0)) = l1.x p0.x + l1.y p0.y
-                sy += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
-                // un-apply RY: RY(-theta)
-                ry(p0, p1, r.cy, -r.sy);
-                ry(l0, l1, r.cy, -r.sy);
-            }
+            for (int j = 0; j < (1 << NB); j++)
+                if (!((j >> i) & 1)) sy = radd(sy, adj_pair(p[j], p[j | (1 << i)], l[j], l[j | (1 << i)], r));
             gy[i].add(sy);
         }
 #pragma unroll
@@ -648,22 +808,12 @@ __device__ void adj_round(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, 
     }
 }
 
-// One RY_q pair of psi and lam in the backward sweep: the pair's share of
-// dE/dtheta_q = Im<lam|Y_q|psi> (Y psi = (-i p1, i p0)), then RY(-theta) on both.
-template <typename T2, typename R>
-__device__ __forceinline__ R adj_pair(T2 &p0, T2 &p1, T2 &l0, T2 &l1, const Rot<R> &r) {
-    const R g = (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
-    ry(p0, p1, r.cy, -r.sy);
-    ry(l0, l1, r.cy, -r.sy);
-    return g;
-}
-
 // adj_round with the NB bits B0 .. B0+NB-1 fixed at compile time (see
 // tile_round_ct for the addressing)
 template <typename R, int B0, int NB>
-__device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T0, const Rot<R> *rot,
-                             Acc<R> (&gy)[3]) {
-    using T2 = typename Cx<R>::T;
+__device__ void adj_round_ct(typename HT<R>::Amp *tp, typename HT<R>::Amp *tl, int T0, const Rot<R> *rot,
+                             RAcc<R> (&gy)[3]) {
+    using T2 = typename HT<R>::Amp;
     const uint32_t nsub = 1u << (T0 - NB);
     for (uint32_t s = threadIdx.x; s < nsub; s += blockDim.x) {
         const uint32_t sb = sw<R>(((s >> B0) << (B0 + NB)) | (s & ((1u << B0) - 1)));
@@ -676,10 +826,10 @@ __device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T
 #pragma unroll
         for (int i = 0; i < NB; i++) {
             const Rot<R> r = rot[i];
-            R sy = 0;
+            auto sy = rzero<typename HT<R>::Real>();
 #pragma unroll
             for (int j = 0; j < (1 << NB); j++)
-                if (!((j >> i) & 1)) sy += adj_pair(p[j], p[j | (1 << i)], l[j], l[j | (1 << i)], r);
+                if (!((j >> i) & 1)) sy = radd(sy, adj_pair(p[j], p[j | (1 << i)], l[j], l[j | (1 << i)], r));
             gy[i].add(sy);
         }
 #pragma unroll
@@ -690,20 +840,12 @@ __device__ void adj_round_ct(typename Cx<R>::T *tp, typename Cx<R>::T *tl, int T
     }
 }
 
-// warp sum in the arithmetic type of the state (fp32 for complex64)
-template <typename R>
-__device__ __forceinline__ R warp_sum_r(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
-k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam,
+k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
                const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
                const __grid_constant__ PassArgs P, double *__restrict__ grad) {
-    using T2 = typename Cx<R>::T;
+    using T2 = typename HT<R>::Amp;
     constexpr int T = tile_bits<R>();
     constexpr int IT = TileRegs<R>::IT;
     constexpr int NW = kThreads / 32;
@@ -740,8 +882,9 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
             }
         }
     };
-    auto add = [&](int slot, R v) {  // lane 0 holds the warp's sum
-        if (lane == 0) gacc[warp][slot] += double(v);
+    using Re = typename HT<R>::Real;
+    auto add = [&](int slot, Re v) {  // lane 0 holds the warp's sum
+        if (lane == 0) gacc[warp][slot] += to_double(v);
     };
     __syncthreads();
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
@@ -779,9 +922,9 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
             // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x)
             // is taken from the same state, then the diagonal is un-applied.
             // Rotated bits below 8 depend on the thread only, bits 8.. on i.
-            R wsum = 0, wreg[reg_bits<R>()];
+            Re wsum = rzero<Re>(), wreg[reg_bits<R>()];
 #pragma unroll
-            for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] = 0;
+            for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] = rzero<Re>();
             auto rz = [&](auto warp_phase) {
                 const T2 pt = pa[threadIdx.x & 255u];
                 const T2 *pw = pc + ((threadIdx.x >> 5) << 4);
@@ -790,52 +933,49 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                     if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
                     T2 a = bp.v[i], b = bl.v[i];
                     if ((czm >> i) & 1) {  // undo the CZ ladder (self-inverse)
-                        a.x = -a.x;
-                        a.y = -a.y;
-                        b.x = -b.x;
-                        b.y = -b.y;
+                        a = aneg(a);
+                        b = aneg(b);
                     }
-                    const R w = b.x * a.y - b.y * a.x;
-                    wsum += w;
+                    const Re w = im_conj_mul(b, a);
+                    wsum = radd(wsum, w);
 #pragma unroll
-                    for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] += ((i >> rb) & 1) ? -w : w;
-                    T2 ph = warp_phase.value ? pw[i] : cmul(pt, pb[i]);
-                    ph.y = -ph.y;  // conjugate
-                    bp.v[i] = cmul(ph, a);
-                    bl.v[i] = cmul(ph, b);
+                    for (int rb = 0; rb < reg_bits<R>(); rb++) wreg[rb] = radd(wreg[rb], ((i >> rb) & 1) ? rneg(w) : w);
+                    const T2 ph = aconj(warp_phase.value ? pw[i] : amul(pt, pb[i]));
+                    bp.v[i] = amul(ph, a);
+                    bl.v[i] = amul(ph, b);
                 }
             };
             if (G.rb0 >= 5) rz(std::true_type{});
             else rz(std::false_type{});
             // sums over the warp with lane-dependent signs (rotated bits 0..4):
             // a Walsh-Hadamard butterfly leaves sum_l (-1)^popc(j & l) w_l in lane j
-            R h = wsum;
+            Re h = wsum;
 #pragma unroll
             for (int b = 0; b < 5; b++) {
-                const R o = __shfl_xor_sync(0xffffffffu, h, 1 << b);
-                h = ((lane >> b) & 1) ? (o - h) : (h + o);
+                const Re o = rshfl_xor(h, 1 << b);
+                h = ((lane >> b) & 1) ? radd(o, rneg(h)) : radd(h, o);
             }
-            R hl[5];
+            Re hl[5];
 #pragma unroll
-            for (int b = 0; b < 5; b++) hl[b] = __shfl_sync(0xffffffffu, h, 1 << b);
-            const R htot = __shfl_sync(0xffffffffu, h, 0);
+            for (int b = 0; b < 5; b++) hl[b] = rshfl(h, 1 << b);
+            const Re htot = rshfl(h, 0);
             for (int r = 0; r < G.nrot; r++) {
                 const int lb = G.rb0 + r;
                 if (lb < 5) {
-                    R v = 0;
+                    Re v = rzero<Re>();
 #pragma unroll
                     for (int b = 0; b < 5; b++)
                         if (lb == b) v = hl[b];
                     add(T + r, v);
                 } else if (lb < 8) {
-                    add(T + r, ((threadIdx.x >> lb) & 1) ? -htot : htot);
+                    add(T + r, ((threadIdx.x >> lb) & 1) ? rneg(htot) : htot);
                 }
             }
 #pragma unroll
             for (int rb = 0; rb < reg_bits<R>(); rb++) {
                 const int lb = 8 + rb;
                 if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
-                add(T + lb - G.rb0, warp_sum_r<R>(wreg[rb]));
+                add(T + lb - G.rb0, warp_sum_r(wreg[rb]));
             }
             // RY gradients and un-rotation of the register-held bits 8..
 #pragma unroll
@@ -844,12 +984,12 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                 if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
                 const Rot<R> r = lr[G.q0 + lb - G.rb0];
                 const int nact = int(sz >> 8);  // registers holding amplitudes (lb < T0, so >= 2)
-                R sy = 0;
+                Re sy = rzero<Re>();
 #pragma unroll
                 for (int i = 0; i < IT; i++)
                     if (!((i >> rb) & 1) && i < nact)
-                        sy += adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r);
-                add(lb - G.rb0, warp_sum_r<R>(sy));
+                        sy = radd(sy, adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r));
+                add(lb - G.rb0, warp_sum_r(sy));
             }
             tile_put<R>(bp, tp, sz);
             tile_put<R>(bl, tl, sz);
@@ -859,30 +999,30 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
         {
             const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
             const Rot<R> *r = lr + G.q0;
-            auto flush_gy = [&](Acc<R> (&gy)[3], int r0, int nb) {
-                for (int i = 0; i < nb; i++) add(r0 + i, warp_sum_r<R>(R(gy[i].value())));
+            auto flush_gy = [&](RAcc<R> (&gy)[3], int r0, int nb) {
+                for (int i = 0; i < nb; i++) add(r0 + i, warp_sum_r(gy[i].get()));
             };
             if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
                 {
-                    Acc<R> gy[3];
+                    RAcc<R> gy[3];
                     adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
                     flush_gy(gy, 0, 3);
                 }
                 __syncthreads();
                 {
-                    Acc<R> gy[3];
+                    RAcc<R> gy[3];
                     adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
                     flush_gy(gy, 3, 3);
                 }
                 __syncthreads();
                 {
-                    Acc<R> gy[3];
+                    RAcc<R> gy[3];
                     adj_round_ct<R, 6, 2>(tp, tl, G.T0, r + 6, gy);
                     flush_gy(gy, 6, 2);
                 }
                 __syncthreads();
             } else if (G.rb0 == 5 && hi == 8) {
-                Acc<R> gy[3];
+                RAcc<R> gy[3];
                 adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
                 flush_gy(gy, 0, 3);
                 __syncthreads();
@@ -895,7 +1035,7 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
                         bits[i] = b0 + i;
                         rr[i] = lr[G.q0 + b0 - G.rb0 + i];
                     }
-                    Acc<R> gy[3];
+                    RAcc<R> gy[3];
                     if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
                     else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
                     else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
@@ -910,8 +1050,8 @@ k_hea_backward(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restric
             for (int i = 0; i < IT; i++) {
                 if (threadIdx.x + uint32_t(i) * kThreads >= sz) continue;
                 const uint64_t x = ta.x0 + uint64_t(i) * ta.stride;
-                psi[I.off + x] = tp[s0 + uint32_t(i) * kThreads];
-                lam[I.off + x] = tl[s0 + uint32_t(i) * kThreads];
+                psi[I.off + x] = (tp[s0 + uint32_t(i) * kThreads]);
+                lam[I.off + x] = (tl[s0 + uint32_t(i) * kThreads]);
             }
         }
         __syncthreads();
@@ -931,29 +1071,26 @@ __global__ void k_hea_prep(const HeaInst *__restrict__ insts, int ninst, int lay
         const int l = e / I.n, q = e % I.n;
         const double th = params[I.param_off + 2 * I.n * l + q];
         const double ph = params[I.param_off + 2 * I.n * l + I.n + q];
+        using Re = typename HT<R>::Real;
         Rot<R> r;
-        r.cy = R(cos(0.5 * th));
-        r.sy = R(sin(0.5 * th));
-        r.cz = R(cos(0.5 * ph));
-        r.sz = R(sin(0.5 * ph));
+        r.cy = rfrom_d<Re>(cos(0.5 * th));
+        r.sy = rfrom_d<Re>(sin(0.5 * th));
+        r.cz = rfrom_d<Re>(cos(0.5 * ph));
+        r.sz = rfrom_d<Re>(sin(0.5 * ph));
         rot[I.rot_off + e] = r;
     }
 }
 
 // every instance to |0...0>
 template <typename R>
-__global__ void k_hea_reset(typename Cx<R>::T *__restrict__ arena, const HeaInst *__restrict__ insts, int ninst) {
+__global__ void k_hea_reset(typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict__ insts, int ninst) {
     const int id = blockIdx.y;
     if (id >= ninst) return;
     const HeaInst I = insts[id];
-    using T2 = typename Cx<R>::T;
+    using Re = typename HT<R>::Real;
     const uint64_t N = uint64_t(1) << I.n;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += uint64_t(gridDim.x) * blockDim.x) {
-        T2 v;
-        v.x = i == 0 ? R(1) : R(0);
-        v.y = 0;
-        arena[I.off + i] = v;
-    }
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += uint64_t(gridDim.x) * blockDim.x)
+        arena[I.off + i] = make_amp(rfrom_i<Re>(i == 0 ? 1 : 0), rzero<Re>());
 }
 
 }  // namespace
@@ -981,6 +1118,7 @@ struct cast_hea {
     cudaGraph_t graph[2] = {nullptr, nullptr};  // [energy][grad]
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     double graph_zz[2] = {0, 0}, graph_hx[2] = {0, 0};
+    bool graph_df[2] = {false, false};  // complex128 graph built in double-float arithmetic
     int grid = 0;
 };
 
@@ -989,7 +1127,7 @@ namespace {
 
 template <typename R>
 cast_status queue_hea(cast_hea *b, bool grad) {
-    using T2 = typename Cx<R>::T;
+    using T2 = typename HT<R>::Amp;  // 8 or 16 bytes per amplitude in the arena
     constexpr int T = tile_bits<R>();
     cudaStream_t st = b->stream;
     T2 *psi = static_cast<T2 *>(b->psi), *lam = static_cast<T2 *>(b->lam);
@@ -1127,6 +1265,8 @@ cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers
         all_prefix.push_back(acc);
         b->pass_tiles[g] = acc;
     }
+    static_assert(sizeof(Rot<DF>) == sizeof(Rot<double>) && tile_bits<DF>() == tile_bits<double>(),
+                  "one complex128 layout for both arithmetics");
     const size_t rot_bytes = (dt == CAST_C64 ? sizeof(Rot<float>) : sizeof(Rot<double>)) * size_t(roff);
     bool ok = cudaMalloc(&b->psi, off * S) == cudaSuccess;
     ok = ok && (!b->with_grad || cudaMalloc(&b->lam, off * S) == cudaSuccess);
@@ -1170,8 +1310,9 @@ static cast_status run_hea(cast_hea *b, const double *params, double zz, double 
     std::memcpy(b->h_params, params, sizeof(double) * b->nparams);
     b->zz = zz;
     b->hx = hx;
-    // the graph bakes in zz and hx; rebuild it when they change
-    if (b->exec[gi] && (b->graph_zz[gi] != zz || b->graph_hx[gi] != hx)) {
+    // the graph bakes in zz, hx and the complex128 arithmetic; rebuild it when they change
+    const bool use_df = b->dt == CAST_C128 && f64_mode() == CAST_F64_EMULATED;
+    if (b->exec[gi] && (b->graph_zz[gi] != zz || b->graph_hx[gi] != hx || b->graph_df[gi] != use_df)) {
         cudaGraphExecDestroy(b->exec[gi]);
         cudaGraphDestroy(b->graph[gi]);
         b->exec[gi] = nullptr;
@@ -1186,7 +1327,9 @@ static cast_status run_hea(cast_hea *b, const double *params, double zz, double 
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             st = cuda_fail(cudaGetLastError(), "cudaStreamBeginCapture");
         } else {
-            st = b->dt == CAST_C64 ? queue_hea<float>(b, grad) : queue_hea<double>(b, grad);
+            st = b->dt == CAST_C64 ? queue_hea<float>(b, grad)
+                 : use_df          ? queue_hea<DF>(b, grad)
+                                   : queue_hea<double>(b, grad);
             cudaGraph_t gph = nullptr;
             cudaError_t e = cudaStreamEndCapture(cap, &gph);
             if (st == CAST_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamEndCapture");
@@ -1196,6 +1339,7 @@ static cast_status run_hea(cast_hea *b, const double *params, double zz, double 
                 b->graph[gi] = gph;
                 b->graph_zz[gi] = zz;
                 b->graph_hx[gi] = hx;
+                b->graph_df[gi] = use_df;
             } else if (gph) {
                 cudaGraphDestroy(gph);
             }

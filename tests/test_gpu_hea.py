@@ -16,6 +16,25 @@ from paper_2503_19894_gb300 import capi
 
 pytestmark = pytest.mark.gpu
 
+# complex128 runs in double-float arithmetic on the FP32 pipe (the default)
+# or on the FP64 pipe; both are checked
+F64_MODES = {"df": "CAST_F64_EMULATED", "fp64": "CAST_F64_NATIVE"}
+
+
+@pytest.fixture
+def f64(request):
+    mode = getattr(request, "param", "df")
+    old = capi.cast_get_f64_mode()
+    capi.cast_set_f64_mode(getattr(capi, F64_MODES[mode]))
+    yield mode
+    capi.cast_set_f64_mode(old)
+
+
+def with_modes(c128_tol, c64_tol):
+    """(dtype, f64 mode, tolerance) cases: complex128 in both arithmetics."""
+    return pytest.mark.parametrize("dtype,f64,tol", [("c128", "df", c128_tol), ("c128", "fp64", c128_tol),
+                                                     ("c64", "df", c64_tol)], indirect=["f64"])
+
 
 def tfim(n, zz, hx):
     return [W.PauliTerm(zz, "ZZ", (i, i + 1)) for i in range(n - 1)] + \
@@ -30,8 +49,8 @@ def split(params, ns, layers):
     return out
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 2e-5)])
-def test_hea_batch_energies(dtype, tol):
+@with_modes(1e-10, 2e-5)
+def test_hea_batch_energies(dtype, f64, tol):
     ns = [4, 7, 11, 12, 13, 16, 18, 20]
     layers, zz, hx = 3, 0.8, 0.5
     b = capi.cast_hea_create(ns, layers, dtype)
@@ -53,8 +72,8 @@ def test_hea_batch_energies(dtype, tol):
     capi.cast_hea_destroy(b)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 5e-5)])
-def test_hea_batch_gradients_vs_parameter_shift(dtype, tol):
+@with_modes(1e-10, 5e-5)
+def test_hea_batch_gradients_vs_parameter_shift(dtype, f64, tol):
     ns = [5, 13, 14]
     layers, zz, hx = 2, 1.0, 0.7
     b = capi.cast_hea_create(ns, layers, dtype, with_grad=True)
@@ -70,7 +89,8 @@ def test_hea_batch_gradients_vs_parameter_shift(dtype, tol):
     capi.cast_hea_destroy(b)
 
 
-def test_hea_matches_single_state_adjoint():
+@pytest.mark.parametrize("f64", ["df", "fp64"], indirect=True)
+def test_hea_matches_single_state_adjoint(f64):
     """The batched adjoint and cast_adjoint_grad on one 15-qubit instance."""
     import paper_2503_19894_gb300 as pkg
     n, layers = 15, 3
@@ -89,8 +109,8 @@ def test_hea_matches_single_state_adjoint():
     capi.cast_hea_destroy(b)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 2e-4)])
-def test_hea_wide_groups_match_single_state_adjoint(dtype, tol):
+@with_modes(1e-10, 2e-4)
+def test_hea_wide_groups_match_single_state_adjoint(dtype, f64, tol):
     """Instances whose later groups rotate 3..7 qubits (bits held in registers
     and the fixed shared-memory rounds) against cast_adjoint_grad, the per-gate
     adjoint checked against parameter shift elsewhere, in the same precision."""
