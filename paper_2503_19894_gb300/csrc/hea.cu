@@ -10,8 +10,13 @@
 // qubits and every rotation of that group is applied while the tile is
 // resident:
 //   group 0      qubits 0 .. T-1            (the tile is contiguous)
-//   group g >= 1 qubits T+(g-1)G .. T+gG-1  (G = T-5), tile = those qubits
-//                plus index bits 0..4 (runs of 32 amplitudes stay coalesced)
+//   group g >= 1 qubits T+(g-1)G .. T+gG-1  (G = T-5, the last group may be
+//                narrower); tile = index bits 0..4 (runs of 32 amplitudes
+//                stay coalesced) plus a window of G consecutive index bits
+//                that holds the group's qubits: those qubits and above, or
+//                for a narrow last group the top G bits.  Every tile of an
+//                instance with n >= T is thus a full 2^T amplitudes; the
+//                window bits that are not rotated are batch bits.
 // A layer is then ~n/G passes.  Rotations on different qubits commute, so the
 // layer "RY on all, RZ on all, CZ ladder" is applied per group as: the RY
 // gates in register rounds of up to three qubits (each thread gathers the 8
@@ -217,11 +222,14 @@ __device__ __forceinline__ Re warp_sum_r(Re v) {
     return v;
 }
 
-// A thread's running sum of Real values: compensated fp32 for complex64,
-// FP64 on the FP64 pipe, double-float for DF; get() returns it as a Real.
+// A running sum of Real values: compensated fp32 for complex64, FP64 on the
+// FP64 pipe, double-float for DF (no FP64 instruction until value()).  A
+// plain aggregate, so it can live in shared memory; zero() or {} clears it.
+// get() returns the sum as a Real, value() as a double.
 template <typename R> struct RAcc;
 template <> struct RAcc<float> {
-    float hi = 0.f, lo = 0.f;
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = lo = 0.f; }
     __device__ __forceinline__ void add(float v) {
         const float s = hi + v;
         const float bb = s - hi;
@@ -229,16 +237,21 @@ template <> struct RAcc<float> {
         hi = s;
     }
     __device__ __forceinline__ float get() const { return hi + lo; }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 template <> struct RAcc<double> {
-    double s = 0.0;
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
     __device__ __forceinline__ void add(double v) { s += v; }
     __device__ __forceinline__ double get() const { return s; }
+    __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct RAcc<DF> {
-    float2 s = make_float2(0.f, 0.f);
+    float2 s;
+    __device__ __forceinline__ void zero() { s = make_float2(0.f, 0.f); }
     __device__ __forceinline__ void add(float2 v) { s = radd(s, v); }
     __device__ __forceinline__ float2 get() const { return s; }
+    __device__ __forceinline__ double value() const { return double(s.x) + double(s.y); }
 };
 
 // one launch = (layer, group); instances with that group and their tile ranges
@@ -258,7 +271,7 @@ struct Geo {
     int rb0;       // first rotated local bit
     int nrot;      // number of rotated qubits (local bits rb0 .. rb0+nrot-1)
     int q0;        // qubit of local bit rb0
-    int p0;        // global position of local bit 5 (g >= 1)
+    int p0;        // global position of local bit 5 (g >= 1): local bits 5 .. T0-1 are global p0 .. p0+T0-6
     bool contiguous;
 };
 
@@ -274,11 +287,12 @@ __host__ __device__ inline Geo geometry(int n, int g, int T) {
     } else {
         const int W = T - 5;
         const int lo = T + (g - 1) * W, hi = (T + g * W < n) ? T + g * W : n;
+        const int w0 = lo + W <= n ? lo : n - W;  // window [w0, w0 + W) holds [lo, hi); w0 >= 5 as n > T
         G.nrot = hi - lo;
-        G.T0 = 5 + G.nrot;
-        G.rb0 = 5;
+        G.T0 = T;
+        G.rb0 = 5 + (lo - w0);
         G.q0 = lo;
-        G.p0 = lo;
+        G.p0 = w0;
         G.contiguous = false;
     }
     return G;
@@ -293,10 +307,10 @@ __host__ __device__ inline int group_count(int n, int T) {
 // global amplitude index of local index l in tile t of group geometry G
 __device__ __forceinline__ uint64_t tile_global(const Geo &G, uint64_t t, uint32_t l) {
     if (G.contiguous) return (t << G.T0) | l;
-    // non-tile bits: 5 .. p0-1 (low part of t) and p0+nrot .. n-1 (high part)
+    // non-tile bits: 5 .. p0-1 (low part of t) and p0+T0-5 .. n-1 (high part)
     const int lowbits = G.p0 - 5;
     const uint64_t tlo = t & ((uint64_t(1) << lowbits) - 1), thi = t >> lowbits;
-    return (thi << (G.p0 + G.nrot)) | (uint64_t(l >> 5) << G.p0) | (tlo << 5) | (l & 31u);
+    return (thi << (G.p0 + G.T0 - 5)) | (uint64_t(l >> 5) << G.p0) | (tlo << 5) | (l & 31u);
 }
 
 __device__ __forceinline__ bool cz_ladder_odd(uint64_t x, int n) {
@@ -669,7 +683,7 @@ k_hea_energy(const typename HT<R>::Amp *__restrict__ arena, const HeaInst *__res
         const typename HT<R>::Amp *sv = arena + I.off;
         const uint32_t sz = 1u << G.T0;
         using Re = typename HT<R>::Real;
-        RAcc<R> acc;
+        RAcc<R> acc{};
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
         TileRegs<R> buf;
         const TileAddr ta = tile_addr(G, t);
@@ -855,7 +869,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
     // per-warp gradient sums, [warp][RY of each rotated qubit, RZ of each]:
     // each warp's lane 0 adds its per-tile sums, no atomics; summed over the
     // warps and sent to global memory when the instance changes
-    __shared__ double gacc[NW][2 * T];
+    __shared__ RAcc<R> gacc[NW][2 * T];
     __shared__ __align__(16) T2 pa[256], pb[16], pc[128];
     int table_inst = -1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -863,7 +877,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = uint64_t(blockIdx.x) * per;
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
-    for (int i = threadIdx.x; i < NW * 2 * T; i += blockDim.x) (&gacc[0][0])[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * 2 * T; i += blockDim.x) (&gacc[0][0])[i].zero();
     int cur = -1, cur_n = 0, cur_q0 = 0, cur_nrot = 0;
     int cur_poff = 0;
     auto flush = [&]() {
@@ -872,8 +886,8 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
             const int r = i % T;
             double v = 0.0;
             for (int w = 0; w < NW; w++) {
-                v += gacc[w][i];
-                gacc[w][i] = 0.0;
+                v += gacc[w][i].value();
+                gacc[w][i].zero();
             }
             if (r < cur_nrot && v != 0.0) {
                 const int q = cur_q0 + r;
@@ -884,7 +898,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
     };
     using Re = typename HT<R>::Real;
     auto add = [&](int slot, Re v) {  // lane 0 holds the warp's sum
-        if (lane == 0) gacc[warp][slot] += to_double(v);
+        if (lane == 0) gacc[warp][slot].add(v);
     };
     __syncthreads();
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
@@ -1004,25 +1018,25 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
             };
             if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
                 {
-                    RAcc<R> gy[3];
+                    RAcc<R> gy[3]{};
                     adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
                     flush_gy(gy, 0, 3);
                 }
                 __syncthreads();
                 {
-                    RAcc<R> gy[3];
+                    RAcc<R> gy[3]{};
                     adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
                     flush_gy(gy, 3, 3);
                 }
                 __syncthreads();
                 {
-                    RAcc<R> gy[3];
+                    RAcc<R> gy[3]{};
                     adj_round_ct<R, 6, 2>(tp, tl, G.T0, r + 6, gy);
                     flush_gy(gy, 6, 2);
                 }
                 __syncthreads();
             } else if (G.rb0 == 5 && hi == 8) {
-                RAcc<R> gy[3];
+                RAcc<R> gy[3]{};
                 adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
                 flush_gy(gy, 0, 3);
                 __syncthreads();
@@ -1035,7 +1049,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                         bits[i] = b0 + i;
                         rr[i] = lr[G.q0 + b0 - G.rb0 + i];
                     }
-                    RAcc<R> gy[3];
+                    RAcc<R> gy[3]{};
                     if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
                     else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
                     else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
