@@ -264,6 +264,7 @@ struct PassArgs {
 };
 
 template <typename R> constexpr int tile_bits() { return HT<R>::T; }
+constexpr int kDfRoundBits = 2;
 
 // Geometry of group g of an n-qubit instance for tile width T.
 struct Geo {
@@ -854,8 +855,16 @@ __device__ void adj_round_ct(typename HT<R>::Amp *tp, typename HT<R>::Amp *tl, i
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1)
+// SR: every RY of the group is un-applied in shared-memory rounds (the
+// registers only carry the tile from HBM through the RZ step), so the kernel
+// fits two CTAs per SM; otherwise the RY gates of register-held bits 8.. are
+// un-applied in registers.  Double-float takes SR (measured: 26-qubit
+// adjoint 454 -> 334 ms), complex64 the register form (70 vs 75 ms).
+template <typename R> constexpr bool bwd_smem_ry() { return std::is_same<R, DF>::value; }
+// bits per generic shared-memory round of the backward
+template <typename R> constexpr int bwd_round_bits() { return std::is_same<R, DF>::value ? kDfRoundBits : 3; }
+template <typename R, bool SR>
+__global__ void __launch_bounds__(kThreads, SR ? 2 : (sizeof(R) == 4 ? 2 : 1))
 k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
                const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
                const __grid_constant__ PassArgs P, double *__restrict__ grad) {
@@ -992,31 +1001,80 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                 add(T + lb - G.rb0, warp_sum_r(wreg[rb]));
             }
             // RY gradients and un-rotation of the register-held bits 8..
+            if constexpr (!SR) {
 #pragma unroll
-            for (int rb = 0; rb < reg_bits<R>(); rb++) {
-                const int lb = 8 + rb;
-                if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
-                const Rot<R> r = lr[G.q0 + lb - G.rb0];
-                const int nact = int(sz >> 8);  // registers holding amplitudes (lb < T0, so >= 2)
-                Re sy = rzero<Re>();
+                for (int rb = 0; rb < reg_bits<R>(); rb++) {
+                    const int lb = 8 + rb;
+                    if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+                    const Rot<R> r = lr[G.q0 + lb - G.rb0];
+                    const int nact = int(sz >> 8);  // registers holding amplitudes (lb < T0, so >= 2)
+                    Re sy = rzero<Re>();
 #pragma unroll
-                for (int i = 0; i < IT; i++)
-                    if (!((i >> rb) & 1) && i < nact)
-                        sy = radd(sy, adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r));
-                add(lb - G.rb0, warp_sum_r(sy));
+                    for (int i = 0; i < IT; i++)
+                        if (!((i >> rb) & 1) && i < nact)
+                            sy = radd(sy, adj_pair(bp.v[i], bp.v[i | (1 << rb)], bl.v[i], bl.v[i | (1 << rb)], r));
+                    add(lb - G.rb0, warp_sum_r(sy));
+                }
             }
             tile_put<R>(bp, tp, sz);
             tile_put<R>(bl, tl, sz);
         }
         __syncthreads();
-        // RY gradients and un-rotation of the rotated bits below 8, through shared memory
+        // RY gradients and un-rotation of the rotated bits below 8 (all of
+        // them for SR), through shared memory
         {
-            const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
+            const int hi = SR ? G.rb0 + G.nrot : (G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8);
             const Rot<R> *r = lr + G.q0;
             auto flush_gy = [&](RAcc<R> (&gy)[3], int r0, int nb) {
                 for (int i = 0; i < nb; i++) add(r0 + i, warp_sum_r(gy[i].get()));
             };
-            if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
+            if (SR && std::is_same<R, float>::value && G.T0 == 12 && G.rb0 == 0 && hi == 12) {
+                // complex64 group 0: four fixed rounds of three bits
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
+                    flush_gy(gy, 0, 3);
+                }
+                __syncthreads();
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
+                    flush_gy(gy, 3, 3);
+                }
+                __syncthreads();
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 6, 3>(tp, tl, G.T0, r + 6, gy);
+                    flush_gy(gy, 6, 3);
+                }
+                __syncthreads();
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 9, 3>(tp, tl, G.T0, r + 9, gy);
+                    flush_gy(gy, 9, 3);
+                }
+                __syncthreads();
+            } else if (SR && std::is_same<R, float>::value && G.rb0 == 5 && hi == 12) {
+                // complex64 full-width group: rounds of three bits from bit 5
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
+                    flush_gy(gy, 0, 3);
+                }
+                __syncthreads();
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 8, 3>(tp, tl, G.T0, r + 3, gy);
+                    flush_gy(gy, 3, 3);
+                }
+                __syncthreads();
+                {
+                    RAcc<R> gy[3]{};
+                    adj_round_ct<R, 11, 1>(tp, tl, G.T0, r + 6, gy);
+                    flush_gy(gy, 6, 1);
+                }
+                __syncthreads();
+            } else if (!SR && G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
                 {
                     RAcc<R> gy[3]{};
                     adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
@@ -1035,14 +1093,15 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                     flush_gy(gy, 6, 2);
                 }
                 __syncthreads();
-            } else if (G.rb0 == 5 && hi == 8) {
+            } else if (!SR && G.rb0 == 5 && hi == 8) {
                 RAcc<R> gy[3]{};
                 adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
                 flush_gy(gy, 0, 3);
                 __syncthreads();
             } else {
-                for (int b0 = G.rb0; b0 < hi; b0 += 3) {
-                    const int nb = hi - b0 < 3 ? hi - b0 : 3;
+                constexpr int NBM = bwd_round_bits<R>();
+                for (int b0 = G.rb0; b0 < hi; b0 += NBM) {
+                    const int nb = hi - b0 < NBM ? hi - b0 : NBM;
                     int bits[3];
                     Rot<R> rr[3];
                     for (int i = 0; i < nb; i++) {
@@ -1050,9 +1109,14 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                         rr[i] = lr[G.q0 + b0 - G.rb0 + i];
                     }
                     RAcc<R> gy[3]{};
-                    if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
-                    else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
-                    else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                    if constexpr (NBM == 3) {
+                        if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
+                        else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
+                        else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                    } else {
+                        if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
+                        else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                    }
                     flush_gy(gy, b0 - G.rb0, nb);
                     __syncthreads();
                 }
@@ -1172,7 +1236,7 @@ cast_status queue_hea(cast_hea *b, bool grad) {
         k_hea_energy<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
     }
     if (grad) {
-        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, bwd_smem_ry<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(2 * sizeof(T2) << T)));
         for (int g = 0; g < b->ngroups_max; g++) {
             if (b->pass_ninst[g] == 0) continue;
@@ -1183,8 +1247,8 @@ cast_status queue_hea(cast_hea *b, bool grad) {
                 if (b->pass_ninst[g] == 0) continue;
                 ProfScope ps(st, std::string("hea_bwd_") + dt_name(b->dt),
                              4.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
-                k_hea_backward<R><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(psi, lam, b->d_inst, rot, pass(l, g),
-                                                                          b->d_out + b->ninst);
+                k_hea_backward<R, bwd_smem_ry<R>()><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
+                    psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
             }
     }
     CAST_CUDA(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * (b->ninst + (grad ? b->nparams : 0)),
