@@ -86,6 +86,15 @@ cast_status cast_sv_set_basis(cast_sv *sv, uint64_t index);
 cast_status cast_sv_copy_to_host(const cast_sv *sv, void *host);
 cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host);
 
+/* Queue the copy of all 2^n amplitudes from host memory on the state's stream
+ * and return without waiting, so that a caller with two states on two
+ * streams can stream one state's next input in while the other computes.
+ * The copy is asynchronous only when `host` is page-locked (cudaHostAlloc or
+ * a pinned torch tensor); the buffer must stay valid and unchanged until the
+ * state's stream has passed the copy (e.g. until a later call on this state
+ * that waits, such as cast_expectation). */
+cast_status cast_sv_copy_from_host_async(cast_sv *sv, const void *host);
+
 /* ------------------------------------------------------------------------
  * Single gates (Eq. 3)
  * ---------------------------------------------------------------------- */

@@ -65,7 +65,7 @@ class cast_pauli_sum(ctypes.Structure):
 
 
 EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
-           "cast_sv_set_basis", "cast_sv_copy_to_host", "cast_sv_copy_from_host",
+           "cast_sv_set_basis", "cast_sv_copy_to_host", "cast_sv_copy_from_host", "cast_sv_copy_from_host_async",
            "cast_apply_gate", "cast_options_default", "cast_apply_circuit", "cast_fuse",
            "cast_opcount", "cast_expectation", "cast_adjoint_grad", "cast_last_error",
            "cast_version", "cast_plan_create", "cast_plan_apply", "cast_plan_info",
@@ -101,6 +101,7 @@ def load(build_if_missing=True):
         "cast_sv_set_basis": (I, [P, U64]),
         "cast_sv_copy_to_host": (I, [P, P]),
         "cast_sv_copy_from_host": (I, [P, P]),
+        "cast_sv_copy_from_host_async": (I, [P, P]),
         "cast_apply_gate": (I, [P, P, I, P]),
         "cast_options_default": (None, [P]),
         "cast_apply_circuit": (I, [P, P, P, P]),
@@ -198,6 +199,19 @@ def cast_sv_copy_from_host(sv, host):
     if arr.size != (1 << n):
         raise ValueError("host buffer size differs from the state's")
     _check(load().cast_sv_copy_from_host(ctypes.c_void_p(sv), ctypes.c_void_p(arr.ctypes.data)))
+
+
+def cast_sv_copy_from_host_async(sv, host):
+    """Queue the host-to-device copy on the state's stream and return.  `host`
+    must already be a contiguous array of the state's amplitude type (no
+    temporary copy is made: the buffer must outlive the queued copy), and
+    page-locked for the copy to run asynchronously."""
+    n, dt, _ = cast_sv_info(sv)
+    if not isinstance(host, np.ndarray) or host.dtype != _amp_np(dt) or not host.flags["C_CONTIGUOUS"]:
+        raise ValueError("host must be a contiguous numpy array of the state's amplitude type")
+    if host.size != (1 << n):
+        raise ValueError("host buffer size differs from the state's")
+    _check(load().cast_sv_copy_from_host_async(ctypes.c_void_p(sv), ctypes.c_void_p(host.ctypes.data)))
 
 
 # ------------------------------------------------------------------ gates

@@ -317,6 +317,13 @@ cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host) {
     return CAST_OK;
 }
 
+cast_status cast_sv_copy_from_host_async(cast_sv *sv, const void *host) {
+    if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
+    if (!host) return fail(CAST_ERR_ARG, "null host buffer");
+    CAST_CUDA(cudaMemcpyAsync(sv->data, host, amp_bytes(sv->dt) << sv->n, cudaMemcpyHostToDevice, sv->stream));
+    return CAST_OK;
+}
+
 static cast_options resolve_options(const cast_options *opt, cast_dtype dt) {
     cast_options o;
     if (opt)

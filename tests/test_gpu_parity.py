@@ -264,6 +264,36 @@ def test_basis_and_copy_roundtrip():
         sv.close()
 
 
+def test_async_copy_double_buffered_on_two_streams():
+    """Two states on two streams: each one's input is queued with
+    cast_sv_copy_from_host_async while the other applies a circuit; every
+    step's <Z_0> and amplitudes equal the synchronous path's."""
+    import torch
+    n = 16
+    gates = W.random_circuit(n, 4, 5)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    svs = []
+    for s in streams:
+        with torch.cuda.stream(s):
+            svs.append(pkg.StateVector(n, "c64", init_index=None))
+    inputs = [torch.from_numpy(W.random_state(n, 10 + i).astype(np.complex64)).pin_memory() for i in range(4)]
+    z0 = [W.PauliTerm(1.0, "Z", (0,))]
+    capi.cast_sv_copy_from_host_async(svs[0].handle, inputs[0].numpy())
+    for i in range(4):
+        cur, nxt = svs[i % 2], svs[(i + 1) % 2]
+        if i + 1 < 4:
+            capi.cast_sv_copy_from_host_async(nxt.handle, inputs[i + 1].numpy())
+        cur.apply_circuit(gates, fusion="adaptive")
+        z = cur.expectation(z0)
+        want = oracle.apply_circuit(inputs[i].numpy().astype(np.complex128), gates)
+        assert abs(z - oracle.expectation(want, z0)) < 1e-5
+        assert np.max(np.abs(cur.to_numpy() - want)) < 1e-5
+    with pytest.raises(ValueError):  # a temporary copy would not outlive the queued copy
+        capi.cast_sv_copy_from_host_async(svs[0].handle, inputs[0].numpy().astype(np.complex128))
+    for sv in svs:
+        sv.close()
+
+
 def test_errors_are_reported_not_raised_on_device():
     sv = pkg.StateVector(4, "c128")
     with pytest.raises(capi.CastError):
