@@ -328,12 +328,17 @@ __device__ __forceinline__ bool cz_ladder_odd(uint64_t x, int n) {
 // bits 0-2 and 6), 6-7 and 5-7 (lanes vary bits 0-3).
 //   complex64:  bit 4 -> slot bit 0, bit 5 -> 1, bit 6 -> 2 and 3
 //   complex128: bits 3, 4, 5 -> slot bits 0, 1, 2
+//   double-float (16-byte elements too, backward rounds of two bits, whose
+//   round on bits 2-3 has lanes varying bits 0, 1, 4): bit 3 -> slot bit 0,
+//   bit 4 -> slot bits 1 and 2, bit 5 -> slot bit 2
 template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
 template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) {
     return l ^ ((l >> 4) & 3u) ^ (((l >> 6) & 1u) * 12u);
 }
 template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
-template <> __device__ __forceinline__ uint32_t sw<DF>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+template <> __device__ __forceinline__ uint32_t sw<DF>(uint32_t l) {
+    return l ^ ((l >> 3) & 1u) ^ (((l >> 4) & 1u) * 6u) ^ (((l >> 5) & 1u) << 2);
+}
 
 // A thread's share of a tile: register i holds local index l = threadIdx.x +
 // 256 i, global index x0 + i * stride (the register index occupies global
