@@ -497,8 +497,8 @@ int sm_count_cached() {
 }
 
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g) {
-    if (tc_eligible(sv, g)) return launch_gate_tc(sv, g);
     if (tcc_eligible(sv, g)) return launch_gate_tcc(sv, g);
+    if (tc_eligible(sv, g)) return launch_gate_tc(sv, g);
     if (df_eligible(sv, g)) return launch_gate_df(sv, g);
     if (sv->dt == CAST_C64) return dispatch<float>(sv, g);
     return dispatch<double>(sv, g);

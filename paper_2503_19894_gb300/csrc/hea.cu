@@ -653,12 +653,6 @@ __device__ __forceinline__ void flush_slots(double *acc, int nslots, double *dst
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // energy contribution of one group: ZZ (group 0 only) and X_q of the group's qubits
 template <typename R>
 __global__ void __launch_bounds__(kThreads)

@@ -164,7 +164,7 @@ cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
-bool tcc_eligible(const cast_sv *sv, const PreparedGate &g);  // dense k = 7, K-chunked (apply_tcc.cu)
+bool tcc_eligible(const cast_sv *sv, const PreparedGate &g);  // dense k = 6, 7, K-chunked (apply_tcc.cu)
 cast_status launch_gate_tcc(cast_sv *sv, const PreparedGate &g);
 int tcc_error_flag_take();          // the chunked kernel's bounded-wait error flag, cleared
 bool tensor_mode_tf32x3();          // cast_set_tensor_mode(CAST_TC_TF32X3) in effect
