@@ -86,9 +86,10 @@ __device__ __forceinline__ float tcc_round(float x) {
 // ninth warp only waits on mbarriers, issues the MMAs and brings in W (k = 7:
 // chunk by chunk into two buffers; k = 6: once, resident).  Both groups drain
 // an accumulator (alternate 32-column blocks, norms exchanged per lane quarter
-// through an mbarrier).  With two accumulators (k = 6) a group drains tile t
-// after it has prepared its first chunk of tile t + 1, so those MMAs run
-// during the epilogue.  Barriers (a = accumulator of the tile, NACC of them):
+// through an mbarrier).  A group drains tile t after it has prepared its first
+// chunk of tile t + 1: with two accumulators (k = 6) those MMAs run during the
+// epilogue; with one (k = 7) they can start as soon as it ends.  Barriers
+// (a = accumulator of the tile, NACC of them):
 //   bar_a[g]  A chunk of group g in TMEM (128 arrivals)     phase: job / 2
 //   bar_b[b]  W chunk in shared buffer b (bulk-copy bytes)   phase: job / 2 (k = 6: all of W, once)
 //   bar_m[b]  MMAs of the chunk in buffer b done (commit)    phase: job / 2
@@ -382,30 +383,17 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
             __syncwarp();
             if (j + 4 < njobs) copy_async(j + 4);
             asm volatile("cp.async.commit_group;" ::: "memory");
-            if constexpr (NACC == 1) {
-                xs += xa + xb;
-                if (c == CHUNKS - 2 + g) {  // this group's last chunk of the tile
-                    if (!epilogue(t, xs)) {
-                        *fail = 1;
-                        break;
-                    }
-                    xs = 0.f;
+            if (c == g && t >= 1) {  // first chunk of tile t queued: drain tile t - 1
+                const float xt = xs;
+                xs = 0.f;
+                if (!epilogue(t - 1, xt)) {
+                    *fail = 1;
+                    break;
                 }
-            } else {
-                if (c == g && t >= 1) {  // first chunk of tile t queued: drain tile t - 1
-                    const float xt = xs;
-                    xs = 0.f;
-                    if (!epilogue(t - 1, xt)) {
-                        *fail = 1;
-                        break;
-                    }
-                }
-                xs += xa + xb;
             }
+            xs += xa + xb;
         }
-        if constexpr (NACC > 1) {
-            if (!*fail && my_tiles > 0 && !epilogue(my_tiles - 1, xs)) *fail = 1;
-        }
+        if (!*fail && my_tiles > 0 && !epilogue(my_tiles - 1, xs)) *fail = 1;
         asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
