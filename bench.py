@@ -572,11 +572,20 @@ def main():
         et = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        # the machine's host-to-device rate for this buffer, one copy alone (outside the timed region)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record(s2)
+        capi.cast_sv_copy_from_host_async(sv2.handle, hv)
+        c1.record(s2)
+        torch.cuda.synchronize()
+        h2d_gbs = round(((1 << n) * S) / (c0.elapsed_time(c1) * 1e-3) / 1e9, 1)
         e2e = {"value": round(step_bytes * a.steps * world / float(et.item()) / 1e9, 2), "unit": "GB/s",
                "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": 8,
                "ms_per_step": round(float(et.item()) / a.steps * 1e3, 2),
                "ms_per_step_parts": {k: round(v / a.steps * 1e3, 2) for k, v in parts.items()},
-               "overlap": "step i+1's input copied while step i computes (2 states, 2 streams)"}
+               "overlap": "step i+1's input copied while step i computes (2 states, 2 streams)",
+               "h2d_gbs_isolated": h2d_gbs}
         sv2.close()
         del host
     sv.close()
