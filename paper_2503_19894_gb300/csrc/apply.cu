@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256)
 k_diag(typename Cx<R>::T *__restrict__ sv, uint64_t N, Targets tg,
        const __grid_constant__ DiagVec<R, K> D) {
     using V = typename Vec16<R>::T;
-    constexpr int A = Vec16<R>::A, UNR = 4;
+    constexpr int A = Vec16<R>::A, UNR = 8;  // vectors in flight per thread (4: 2% slower, 16: 55% slower)
     V *vp = reinterpret_cast<V *>(sv);
     const uint64_t nvec = N / A;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
