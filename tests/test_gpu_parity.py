@@ -332,12 +332,15 @@ def tensor_mode():
 @pytest.mark.parametrize("k", [4, 5, 6, 7])
 def test_tensor_core_gate_matches_oracle(k, tensor_mode):
     """3xTF32 tcgen05 path (complex64, k = 4..7, n >= k + 7): every placement,
-    a single-tile state and multi-tile states with ragged CTA shares."""
+    a single-tile state, states with one tile per CTA, and at 22 qubits
+    several tiles per CTA with ragged shares (the pipelines that carry a
+    tile's accumulator or epilogue into the next tile)."""
     capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
     rng = np.random.default_rng(500 + k)
-    for n in (k + 7, k + 8, 16, 19):
+    for n in (k + 7, k + 8, 16, 19, 22):
         psi0 = W.random_state(n, n + k)
-        for placement in ("low", "high", "mixed", "mixed", "mixed"):
+        places = ("low", "high", "mixed", "mixed", "mixed") if n < 22 else ("low", "mixed")
+        for placement in places:
             qs = W.sweep_targets(n, k, placement, rng)
             u = W.haar_unitary(k, rng)
             got = run_gate(n, "c64", psi0, qs, u)
