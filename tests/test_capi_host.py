@@ -159,6 +159,12 @@ def test_validation_before_any_cuda_call():
     for gates in bad:
         assert _err(lambda: capi.cast_fuse(4, gates, np.zeros(2))) == 1
     assert "qubit" in capi.cast_last_error() or "size" in capi.cast_last_error()
+    # state calls reject a null handle before touching the device
+    lib = capi.load()
+    host = np.zeros(16, dtype=np.complex64)
+    assert lib.cast_sv_copy_from_host_async(None, host.ctypes.data) == 1
+    assert lib.cast_sv_copy_from_host(None, host.ctypes.data) == 1
+    assert lib.cast_sv_set_basis(None, 0) == 1
 
 
 def test_fuse_reports_required_capacity():
