@@ -499,14 +499,14 @@ __device__ void tile_round_ct(typename HT<R>::Amp *tile, int T0, const Rot<R> *r
 template <typename R> constexpr int reg_bits() { return tile_bits<R>() - 8; }
 
 template <typename R, typename Regs>
-__device__ __forceinline__ void reg_rotations(Regs &b, const Geo &G, const Rot<R> *rots) {
+__device__ __forceinline__ void reg_rotations(Regs &b, const Geo &G, int T0, const Rot<R> *rots) {
     constexpr int IT = 1 << reg_bits<R>();
 #pragma unroll
     for (int rb = 0; rb < reg_bits<R>(); rb++) {
         const int lb = 8 + rb;
-        if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+        if (lb >= T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
         const Rot<R> r = rots[G.q0 + lb - G.rb0];
-        const int nact = 1 << (G.T0 - 8);  // registers holding amplitudes
+        const int nact = 1 << (T0 - 8);  // registers holding amplitudes
 #pragma unroll
         for (int i = 0; i < IT; i++)
             if (!((i >> rb) & 1) && i < nact) fwd_pair(b.v[i], b.v[i | (1 << rb)], r);
@@ -517,21 +517,21 @@ __device__ __forceinline__ void reg_rotations(Regs &b, const Geo &G, const Rot<R
 // registers): fixed rounds for the full-width groups, else rounds of three
 // with runtime bit positions.
 template <typename R>
-__device__ void smem_rotations(typename HT<R>::Amp *tile, const Geo &G, const Rot<R> *rots) {
+__device__ __forceinline__ void smem_rotations(typename HT<R>::Amp *tile, const Geo &G, int T0, const Rot<R> *rots) {
     const int hi = G.rb0 + G.nrot < 8 ? G.rb0 + G.nrot : 8;
     if (G.rb0 >= hi) return;
     const Rot<R> *r = rots + G.q0;  // RY/RZ entries of the group's rotated qubits, in order
-    if (G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
-        tile_round_ct<R, 0, 3>(tile, G.T0, r);
+    if (T0 >= 8 && G.rb0 == 0 && hi == 8) {
+        tile_round_ct<R, 0, 3>(tile, T0, r);
         __syncthreads();
-        tile_round_ct<R, 3, 3>(tile, G.T0, r + 3);
+        tile_round_ct<R, 3, 3>(tile, T0, r + 3);
         __syncthreads();
-        tile_round_ct<R, 6, 2>(tile, G.T0, r + 6);
+        tile_round_ct<R, 6, 2>(tile, T0, r + 6);
         __syncthreads();
         return;
     }
     if (G.rb0 == 5 && hi == 8) {
-        tile_round_ct<R, 5, 3>(tile, G.T0, r);
+        tile_round_ct<R, 5, 3>(tile, T0, r);
         __syncthreads();
         return;
     }
@@ -543,9 +543,9 @@ __device__ void smem_rotations(typename HT<R>::Amp *tile, const Geo &G, const Ro
             bits[i] = b0 + i;
             rr[i] = rots[G.q0 + b0 - G.rb0 + i];
         }
-        if (nb == 3) tile_round<R, 3>(tile, G.T0, bits, rr);
-        else if (nb == 2) tile_round<R, 2>(tile, G.T0, bits, rr);
-        else tile_round<R, 1>(tile, G.T0, bits, rr);
+        if (nb == 3) tile_round<R, 3>(tile, T0, bits, rr);
+        else if (nb == 2) tile_round<R, 2>(tile, T0, bits, rr);
+        else tile_round<R, 1>(tile, T0, bits, rr);
         __syncthreads();
     }
 }
@@ -574,7 +574,10 @@ __device__ __forceinline__ void tile_put(const TileRegs<R> &b, typename HT<R>::A
         if (threadIdx.x + uint32_t(i) * kThreads < sz) tile[s0 + uint32_t(i) * kThreads] = b.v[i];
 }
 
-template <typename R>
+// FULL: every tile of the pass has 2^T amplitudes (all its instances have
+// n >= T), so the tile size is a compile-time constant and the per-element
+// guards fold away
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 2)
 k_hea_forward(typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict__ insts,
               const Rot<R> *__restrict__ rot, const __grid_constant__ PassArgs P) {
@@ -595,11 +598,12 @@ k_hea_forward(typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict
     HeaInst I = insts[P.inst[k]];
     Geo G = geometry(I.n, P.group, T);
     uint64_t t = t_begin - P.prefix[k];
-    tile_load<R>(buf, arena + I.off, tile_addr(G, t), 1u << G.T0);
+    tile_load<R>(buf, arena + I.off, tile_addr(G, t), FULL ? (1u << T) : (1u << G.T0));
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
-        const uint32_t sz = 1u << G.T0;
+        const int T0 = FULL ? T : G.T0;
+        const uint32_t sz = 1u << T0;
         const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
-        reg_rotations<R>(buf, G, lr);
+        reg_rotations<R>(buf, G, T0, lr);
         tile_put<R>(buf, tile, sz);
         const HeaInst Ic = I;
         const Geo Gc = G;
@@ -618,13 +622,13 @@ k_hea_forward(typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict
             I = insts[P.inst[k]];
             G = geometry(I.n, P.group, T);
             t = gt + 1 - P.prefix[k];
-            tile_load<R>(buf, arena + I.off, tile_addr(G, t), 1u << G.T0);
+            tile_load<R>(buf, arena + I.off, tile_addr(G, t), FULL ? (1u << T) : (1u << G.T0));
         }
-        smem_rotations<R>(tile, Gc, lr);
+        smem_rotations<R>(tile, Gc, T0, lr);
         // the group's RZ gates as one diagonal, then (last group) the CZ ladder
         const TileAddr a = tile_addr(Gc, tc);
         const uint32_t czm = (P.group == Ic.ngroups - 1)
-                                 ? cz_mask(a, Gc.T0 > 8 ? Gc.T0 - 8 : 0, Ic.n) : 0u;
+                                 ? cz_mask(a, T0 > 8 ? T0 - 8 : 0, Ic.n) : 0u;
         const uint32_t s0 = sw<R>(threadIdx.x);
         typename HT<R>::Amp *sv = arena + Ic.off;
         auto store = [&](auto warp_phase) {
@@ -866,7 +870,7 @@ template <typename R> constexpr bool bwd_smem_ry() { return std::is_same<R, DF>:
 template <typename R> constexpr bool bwd_prefetch() { return std::is_same<R, float>::value; }
 // bits per generic shared-memory round of the backward
 template <typename R> constexpr int bwd_round_bits() { return std::is_same<R, DF>::value ? kDfRoundBits : 3; }
-template <typename R, bool SR, bool PF>
+template <typename R, bool SR, bool PF, bool FULL>
 __global__ void __launch_bounds__(kThreads, SR ? 2 : (sizeof(R) == 4 ? 2 : 1))
 k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
                const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
@@ -919,8 +923,8 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
         const HeaInst I2 = insts[P.inst[k2]];
         const Geo G2 = geometry(I2.n, P.group, T);
         const TileAddr ta2 = tile_addr(G2, g2 - P.prefix[k2]);
-        tile_load<R>(bp, psi + I2.off, ta2, 1u << G2.T0);
-        tile_load<R>(bl, lam + I2.off, ta2, 1u << G2.T0);
+        tile_load<R>(bp, psi + I2.off, ta2, FULL ? (1u << T) : (1u << G2.T0));
+        tile_load<R>(bl, lam + I2.off, ta2, FULL ? (1u << T) : (1u << G2.T0));
     };
     if (PF && t_begin < t_end) fetch(t_begin);
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
@@ -939,7 +943,8 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
             cur_poff = I.param_off;
         }
         const uint64_t t = gt - P.prefix[k];
-        const uint32_t sz = 1u << G.T0;
+        const int T0 = FULL ? T : G.T0;
+        const uint32_t sz = 1u << T0;
         const bool last = P.group == I.ngroups - 1;
         const Rot<R> *lr = rot + I.rot_off + size_t(P.layer) * I.n;
         if (int(gt - t) != table_inst) {  // new instance: its RZ phase tables
@@ -954,7 +959,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                 tile_load<R>(bp, psi + I.off, ta, sz);
                 tile_load<R>(bl, lam + I.off, ta, sz);
             }
-            const uint32_t czm = last ? cz_mask(ta, G.T0 > 8 ? G.T0 - 8 : 0, I.n) : 0u;
+            const uint32_t czm = last ? cz_mask(ta, T0 > 8 ? T0 - 8 : 0, I.n) : 0u;
             // the group's RZ gates act last in the layer and commute: every
             // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x)
             // is taken from the same state, then the diagonal is un-applied.
@@ -1011,7 +1016,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
 #pragma unroll
             for (int rb = 0; rb < reg_bits<R>(); rb++) {
                 const int lb = 8 + rb;
-                if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+                if (lb >= T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
                 add(T + lb - G.rb0, warp_sum_r(wreg[rb]));
             }
             // RY gradients and un-rotation of the register-held bits 8..
@@ -1019,7 +1024,7 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
 #pragma unroll
                 for (int rb = 0; rb < reg_bits<R>(); rb++) {
                     const int lb = 8 + rb;
-                    if (lb >= G.T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
+                    if (lb >= T0 || lb < G.rb0 || lb >= G.rb0 + G.nrot) continue;
                     const Rot<R> r = lr[G.q0 + lb - G.rb0];
                     const int nact = int(sz >> 8);  // registers holding amplitudes (lb < T0, so >= 2)
                     Re sy = rzero<Re>();
@@ -1043,29 +1048,29 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
             auto flush_gy = [&](RAcc<R> (&gy)[3], int r0, int nb) {
                 for (int i = 0; i < nb; i++) add(r0 + i, warp_sum_r(gy[i].get()));
             };
-            if (SR && std::is_same<R, float>::value && G.T0 == 12 && G.rb0 == 0 && hi == 12) {
+            if (SR && std::is_same<R, float>::value && T0 == 12 && G.rb0 == 0 && hi == 12) {
                 // complex64 group 0: four fixed rounds of three bits
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
+                    adj_round_ct<R, 0, 3>(tp, tl, T0, r, gy);
                     flush_gy(gy, 0, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
+                    adj_round_ct<R, 3, 3>(tp, tl, T0, r + 3, gy);
                     flush_gy(gy, 3, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 6, 3>(tp, tl, G.T0, r + 6, gy);
+                    adj_round_ct<R, 6, 3>(tp, tl, T0, r + 6, gy);
                     flush_gy(gy, 6, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 9, 3>(tp, tl, G.T0, r + 9, gy);
+                    adj_round_ct<R, 9, 3>(tp, tl, T0, r + 9, gy);
                     flush_gy(gy, 9, 3);
                 }
                 __syncthreads();
@@ -1073,44 +1078,44 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                 // complex64 full-width group: rounds of three bits from bit 5
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
+                    adj_round_ct<R, 5, 3>(tp, tl, T0, r, gy);
                     flush_gy(gy, 0, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 8, 3>(tp, tl, G.T0, r + 3, gy);
+                    adj_round_ct<R, 8, 3>(tp, tl, T0, r + 3, gy);
                     flush_gy(gy, 3, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 11, 1>(tp, tl, G.T0, r + 6, gy);
+                    adj_round_ct<R, 11, 1>(tp, tl, T0, r + 6, gy);
                     flush_gy(gy, 6, 1);
                 }
                 __syncthreads();
-            } else if (!SR && G.T0 >= 8 && G.rb0 == 0 && hi == 8) {
+            } else if (!SR && T0 >= 8 && G.rb0 == 0 && hi == 8) {
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 0, 3>(tp, tl, G.T0, r, gy);
+                    adj_round_ct<R, 0, 3>(tp, tl, T0, r, gy);
                     flush_gy(gy, 0, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 3, 3>(tp, tl, G.T0, r + 3, gy);
+                    adj_round_ct<R, 3, 3>(tp, tl, T0, r + 3, gy);
                     flush_gy(gy, 3, 3);
                 }
                 __syncthreads();
                 {
                     RAcc<R> gy[3]{};
-                    adj_round_ct<R, 6, 2>(tp, tl, G.T0, r + 6, gy);
+                    adj_round_ct<R, 6, 2>(tp, tl, T0, r + 6, gy);
                     flush_gy(gy, 6, 2);
                 }
                 __syncthreads();
             } else if (!SR && G.rb0 == 5 && hi == 8) {
                 RAcc<R> gy[3]{};
-                adj_round_ct<R, 5, 3>(tp, tl, G.T0, r, gy);
+                adj_round_ct<R, 5, 3>(tp, tl, T0, r, gy);
                 flush_gy(gy, 0, 3);
                 __syncthreads();
             } else {
@@ -1125,12 +1130,12 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
                     }
                     RAcc<R> gy[3]{};
                     if constexpr (NBM == 3) {
-                        if (nb == 3) adj_round<R, 3>(tp, tl, G.T0, bits, rr, gy);
-                        else if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
-                        else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                        if (nb == 3) adj_round<R, 3>(tp, tl, T0, bits, rr, gy);
+                        else if (nb == 2) adj_round<R, 2>(tp, tl, T0, bits, rr, gy);
+                        else adj_round<R, 1>(tp, tl, T0, bits, rr, gy);
                     } else {
-                        if (nb == 2) adj_round<R, 2>(tp, tl, G.T0, bits, rr, gy);
-                        else adj_round<R, 1>(tp, tl, G.T0, bits, rr, gy);
+                        if (nb == 2) adj_round<R, 2>(tp, tl, T0, bits, rr, gy);
+                        else adj_round<R, 1>(tp, tl, T0, bits, rr, gy);
                     }
                     flush_gy(gy, b0 - G.rb0, nb);
                     __syncthreads();
@@ -1206,6 +1211,7 @@ struct cast_hea {
     std::vector<int> pass_ninst;            // per group
     std::vector<size_t> pass_inst_off, pass_prefix_off;
     std::vector<uint64_t> pass_tiles;
+    std::vector<char> pass_full;            // every tile of the pass is 2^T amplitudes
     int ngroups_max = 0;
     double zz = 0, hx = 0;
     cudaGraph_t graph[2] = {nullptr, nullptr};  // [energy][grad]
@@ -1243,7 +1249,8 @@ cast_status queue_hea(cast_hea *b, bool grad) {
         for (int g = 0; g < b->ngroups_max; g++) {
             if (b->pass_ninst[g] == 0) continue;
             ProfScope ps(st, std::string("hea_fwd_") + dt_name(b->dt), 2.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
-            k_hea_forward<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, rot, pass(l, g));
+            if (b->pass_full[g]) k_hea_forward<R, true><<<G, kThreads, 0, st>>>(psi, b->d_inst, rot, pass(l, g));
+            else k_hea_forward<R, false><<<G, kThreads, 0, st>>>(psi, b->d_inst, rot, pass(l, g));
         }
     for (int g = 0; g < b->ngroups_max; g++) {
         if (b->pass_ninst[g] == 0) continue;
@@ -1251,7 +1258,10 @@ cast_status queue_hea(cast_hea *b, bool grad) {
         k_hea_energy<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
     }
     if (grad) {
-        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, bwd_smem_ry<R>(), bwd_prefetch<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        constexpr bool SR = bwd_smem_ry<R>(), PF = bwd_prefetch<R>();
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, PF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(2 * sizeof(T2) << T)));
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, PF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(2 * sizeof(T2) << T)));
         for (int g = 0; g < b->ngroups_max; g++) {
             if (b->pass_ninst[g] == 0) continue;
@@ -1262,8 +1272,12 @@ cast_status queue_hea(cast_hea *b, bool grad) {
                 if (b->pass_ninst[g] == 0) continue;
                 ProfScope ps(st, std::string("hea_bwd_") + dt_name(b->dt),
                              4.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
-                k_hea_backward<R, bwd_smem_ry<R>(), bwd_prefetch<R>()><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
-                    psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
+                if (b->pass_full[g])
+                    k_hea_backward<R, SR, PF, true><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
+                        psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
+                else
+                    k_hea_backward<R, SR, PF, false><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
+                        psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
             }
     }
     CAST_CUDA(cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * (b->ninst + (grad ? b->nparams : 0)),
@@ -1343,6 +1357,7 @@ cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers
     std::vector<uint64_t> all_prefix;
     b->pass_ninst.assign(b->ngroups_max, 0);
     b->pass_tiles.assign(b->ngroups_max, 0);
+    b->pass_full.assign(b->ngroups_max, 1);
     for (int g = 0; g < b->ngroups_max; g++) {
         b->pass_inst_off.push_back(all_inst.size());
         b->pass_prefix_off.push_back(all_prefix.size());
@@ -1350,6 +1365,7 @@ cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers
         for (int i = 0; i < n_instances; i++) {
             if (g >= b->inst[i].ngroups) continue;
             const Geo Gm = geometry(b->inst[i].n, g, T);
+            if (Gm.T0 != T) b->pass_full[g] = 0;
             all_inst.push_back(i);
             all_prefix.push_back(acc);
             acc += uint64_t(1) << (b->inst[i].n - Gm.T0);
