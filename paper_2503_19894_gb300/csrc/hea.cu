@@ -658,7 +658,7 @@ __device__ __forceinline__ void flush_slots(double *acc, int nslots, double *dst
 }
 
 // energy contribution of one group: ZZ (group 0 only) and X_q of the group's qubits
-template <typename R>
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_hea_energy(const typename HT<R>::Amp *__restrict__ arena, const HeaInst *__restrict__ insts,
              const __grid_constant__ PassArgs P, double zz, double hx, double *__restrict__ energy) {
@@ -685,7 +685,7 @@ k_hea_energy(const typename HT<R>::Amp *__restrict__ arena, const HeaInst *__res
         const Geo G = geometry(I.n, P.group, T);
         const uint64_t t = gt - P.prefix[k];
         const typename HT<R>::Amp *sv = arena + I.off;
-        const uint32_t sz = 1u << G.T0;
+        const uint32_t sz = FULL ? (1u << T) : (1u << G.T0);
         using Re = typename HT<R>::Real;
         RAcc<R> acc{};
         const uint64_t zmask = I.n > 1 ? ((uint64_t(1) << (I.n - 1)) - 1) : 0;
@@ -725,7 +725,7 @@ k_hea_energy(const typename HT<R>::Amp *__restrict__ arena, const HeaInst *__res
 }
 
 // lam = H psi for one group (group 0 writes, the others add)
-template <typename R>
+template <typename R, bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_hea_lambda(const typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
              const HeaInst *__restrict__ insts, const __grid_constant__ PassArgs P, double zz, double hx) {
@@ -741,7 +741,7 @@ k_hea_lambda(const typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *_
         const HeaInst I = insts[P.inst[k]];
         const Geo G = geometry(I.n, P.group, T);
         const uint64_t t = gt - P.prefix[k];
-        const uint32_t sz = 1u << G.T0;
+        const uint32_t sz = FULL ? (1u << T) : (1u << G.T0);
         const TileAddr ta = tile_addr(G, t);
         {
             TileRegs<R> buf;
@@ -1255,7 +1255,8 @@ cast_status queue_hea(cast_hea *b, bool grad) {
     for (int g = 0; g < b->ngroups_max; g++) {
         if (b->pass_ninst[g] == 0) continue;
         ProfScope ps(st, std::string("hea_energy_") + dt_name(b->dt), sizeof(T2) * double(b->pass_tiles[g] << T), 0);
-        k_hea_energy<R><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
+        if (b->pass_full[g]) k_hea_energy<R, true><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
+        else k_hea_energy<R, false><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
     }
     if (grad) {
         constexpr bool SR = bwd_smem_ry<R>(), PF = bwd_prefetch<R>();
@@ -1265,7 +1266,8 @@ cast_status queue_hea(cast_hea *b, bool grad) {
                                        int(2 * sizeof(T2) << T)));
         for (int g = 0; g < b->ngroups_max; g++) {
             if (b->pass_ninst[g] == 0) continue;
-            k_hea_lambda<R><<<G, kThreads, 0, st>>>(psi, lam, b->d_inst, pass(0, g), b->zz, b->hx);
+            if (b->pass_full[g]) k_hea_lambda<R, true><<<G, kThreads, 0, st>>>(psi, lam, b->d_inst, pass(0, g), b->zz, b->hx);
+            else k_hea_lambda<R, false><<<G, kThreads, 0, st>>>(psi, lam, b->d_inst, pass(0, g), b->zz, b->hx);
         }
         for (int l = b->layers - 1; l >= 0; l--)
             for (int g = b->ngroups_max - 1; g >= 0; g--) {
