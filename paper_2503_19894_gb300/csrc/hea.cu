@@ -864,13 +864,9 @@ __device__ void adj_round_ct(typename HT<R>::Amp *tp, typename HT<R>::Amp *tl, i
 // un-applied in registers.  Double-float takes SR (measured: 26-qubit
 // adjoint 454 -> 334 ms), complex64 the register form (70 vs 75 ms).
 template <typename R> constexpr bool bwd_smem_ry() { return std::is_same<R, DF>::value; }
-// PF: the next tile's psi and lam are loaded into registers as soon as the
-// current tile is parked in shared memory, in flight during its rounds
-// (complex64: 26-qubit adjoint 70.5 -> 66.3 ms; no gain for double-float)
-template <typename R> constexpr bool bwd_prefetch() { return std::is_same<R, float>::value; }
 // bits per generic shared-memory round of the backward
 template <typename R> constexpr int bwd_round_bits() { return std::is_same<R, DF>::value ? kDfRoundBits : 3; }
-template <typename R, bool SR, bool PF, bool FULL>
+template <typename R, bool SR, bool FULL>
 __global__ void __launch_bounds__(kThreads, SR ? 2 : (sizeof(R) == 4 ? 2 : 1))
 k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__restrict__ lam,
                const HeaInst *__restrict__ insts, const Rot<R> *__restrict__ rot,
@@ -917,16 +913,6 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
         if (lane == 0) gacc[warp][slot].add(v);
     };
     __syncthreads();
-    TileRegs<R> bp, bl;  // psi and lam of the thread's share of a tile
-    auto fetch = [&](uint64_t g2) {
-        const int k2 = find_inst(P, g2);
-        const HeaInst I2 = insts[P.inst[k2]];
-        const Geo G2 = geometry(I2.n, P.group, T);
-        const TileAddr ta2 = tile_addr(G2, g2 - P.prefix[k2]);
-        tile_load<R>(bp, psi + I2.off, ta2, FULL ? (1u << T) : (1u << G2.T0));
-        tile_load<R>(bl, lam + I2.off, ta2, FULL ? (1u << T) : (1u << G2.T0));
-    };
-    if (PF && t_begin < t_end) fetch(t_begin);
     for (uint64_t gt = t_begin; gt < t_end; gt++) {
         const int k = find_inst(P, gt);
         const int id = P.inst[k];
@@ -955,10 +941,9 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
         const TileAddr ta = tile_addr(G, t);
         {
             // psi and lam of the thread's share, both in flight together
-            if (!PF) {
-                tile_load<R>(bp, psi + I.off, ta, sz);
-                tile_load<R>(bl, lam + I.off, ta, sz);
-            }
+            TileRegs<R> bp, bl;
+            tile_load<R>(bp, psi + I.off, ta, sz);
+            tile_load<R>(bl, lam + I.off, ta, sz);
             const uint32_t czm = last ? cz_mask(ta, T0 > 8 ? T0 - 8 : 0, I.n) : 0u;
             // the group's RZ gates act last in the layer and commute: every
             // dE/dphi_q = Im<lam|Z_q|psi> = sum_x (1 - 2 x_q) Im(conj(lam_x) psi_x)
@@ -1038,7 +1023,6 @@ k_hea_backward(typename HT<R>::Amp *__restrict__ psi, typename HT<R>::Amp *__res
             tile_put<R>(bp, tp, sz);
             tile_put<R>(bl, tl, sz);
         }
-        if (PF && gt + 1 < t_end) fetch(gt + 1);
         __syncthreads();
         // RY gradients and un-rotation of the rotated bits below 8 (all of
         // them for SR), through shared memory
@@ -1259,10 +1243,10 @@ cast_status queue_hea(cast_hea *b, bool grad) {
         else k_hea_energy<R, false><<<G, kThreads, 0, st>>>(psi, b->d_inst, pass(0, g), b->zz, b->hx, b->d_out);
     }
     if (grad) {
-        constexpr bool SR = bwd_smem_ry<R>(), PF = bwd_prefetch<R>();
-        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, PF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        constexpr bool SR = bwd_smem_ry<R>();
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(2 * sizeof(T2) << T)));
-        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, PF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CAST_CUDA(cudaFuncSetAttribute(k_hea_backward<R, SR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(2 * sizeof(T2) << T)));
         for (int g = 0; g < b->ngroups_max; g++) {
             if (b->pass_ninst[g] == 0) continue;
@@ -1275,10 +1259,10 @@ cast_status queue_hea(cast_hea *b, bool grad) {
                 ProfScope ps(st, std::string("hea_bwd_") + dt_name(b->dt),
                              4.0 * sizeof(T2) * double(b->pass_tiles[g] << T), 0);
                 if (b->pass_full[g])
-                    k_hea_backward<R, SR, PF, true><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
+                    k_hea_backward<R, SR, true><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
                         psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
                 else
-                    k_hea_backward<R, SR, PF, false><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
+                    k_hea_backward<R, SR, false><<<G, kThreads, 2 * sizeof(T2) << T, st>>>(
                         psi, lam, b->d_inst, rot, pass(l, g), b->d_out + b->ninst);
             }
     }
