@@ -376,7 +376,11 @@ cast_status cast_adjoint_grad(cast_sv *psi, cast_sv *lam, const cast_circuit *c,
  * complex128), so a layer costs ~n/(T-5) passes over the states instead of
  * 3n - 1; all instances share each launch, and the launch sequence is
  * captured once in a CUDA graph and replayed for every parameter set.
- * with_grad allocates the second state arena that adjoint gradients need. */
+ * with_grad allocates the second state arena that adjoint gradients need.
+ * A CAST_C128 batch computes in the arithmetic cast_set_f64_mode selects when
+ * a call builds its graph (double-float by default: the arenas then hold
+ * (hi, lo) float pairs, 16 bytes per amplitude like complex128); a later
+ * mode change rebuilds the graph at the next call. */
 typedef struct cast_hea cast_hea;
 
 cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers, cast_dtype dt,
