@@ -172,7 +172,7 @@ def roofline(profile, mp, src, launches_per_step_kind="sustained"):
     # arithmetic intensity against the ridge of the unit that does the work
     sm_mhz = mp.get("sm_max_mhz", 2070.0)
     fp32_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    fp64_tflops = 1.01  # measured FFMA64 rate on this GB300
+    fp64_tflops = 1.01  # FP64 FMA rate measured on GB300 with a dependent-FMA loop (1.01 TFLOP/s)
     alu_peak = fp64_tflops if top["name"].endswith("c128") else fp32_tflops
     alu_t = per_launch_flops / alu_peak / 1e12
     mem_t = per_launch_bytes / (mp["hbm_gbs"] * 1e9)

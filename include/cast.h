@@ -48,7 +48,7 @@ typedef enum {
     CAST_ERR_OOM = 2,         /* device or pinned-host allocation failed */
     CAST_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     CAST_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
-    CAST_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+    CAST_ERR_UNSUPPORTED = 5  /* valid request the library does not serve */
 } cast_status;
 
 /* Opaque state-vector handle. */
@@ -406,7 +406,7 @@ cast_status cast_hea_destroy(cast_hea *b);
 /* Thread-local description of the last failure on this host thread. */
 const char *cast_last_error(void);
 
-/* Version string of this build. */
+/* Version string of the library. */
 const char *cast_version(void);
 
 #ifdef __cplusplus

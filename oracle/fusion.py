@@ -1,7 +1,9 @@
 """Reference agglomerative gate fusion (Section IV, Algorithm 1), in plain Python.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Written from the paper's
-description, step by step, with the readings recorded in the design doc:
+description, step by step, with these readings where the text is silent or
+inconsistent (MoveBlock moves a block only when all of its slots below are
+empty; a fused gate may reach, not only stay below, the size cap k):
 
 CircuitTile (Section IV-A): a list of rows; each row has one slot per qubit,
 holding a GateBlock or None.  A gate is appended as a new block in the first
