@@ -329,10 +329,15 @@ cast_status cast_expectation(const cast_sv *sv, const cast_pauli_sum *h, double 
  * routine.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  The state's device must be current.
+ *     before any stream capture.  The state's device must be current.  The
+ *     address is kept for the process's life: after cudaDeviceReset it is
+ *     stale, and this call must not be used again.
  *   - A Pauli sum needs 1 + (launches x blocks) doubles, one launch per
  *     32 terms sharing an x_mask and 4 blocks per SM (608 on a 152-SM GB300,
- *     so up to 107 launches); larger sums get CAST_ERR_ARG with the sizes.
+ *     so up to 107 launches); larger sums get CAST_ERR_ARG, with the launch
+ *     and block counts in the message.
+ *   - Like cast_expectation it returns CAST_ERR_TIMEOUT when earlier work on
+ *     the state's stream gave up a bounded wait (the value is then void).
  *   - All calls share the array and it keeps the last call's contents; each
  *     call writes every value it reads, so nothing needs clearing, but calls
  *     whose GPU work overlaps (e.g. on two streams) race and may return wrong

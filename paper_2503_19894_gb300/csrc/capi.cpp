@@ -163,16 +163,14 @@ constexpr size_t kResultSlots = 16;
 // Queue <psi|H|psi> into the first result slot of sv->partials.
 cast_status queue_expectation(cast_sv *sv, const cast_pauli_sum *h) {
     PauliGroups G = group_terms(h);
-    const int B = reduce_grid_blocks();
-    size_t slots = 0;
-    for (size_t g = 0; g < G.xm.size(); g++) slots += (G.c[g].size() + 31) / 32;
-    if (slots == 0) {
+    const size_t need = pauli_partials_needed(G);
+    if (need == 0) {
         cast_status st = ensure_dev(sv, sv->partials, 4096 * sizeof(double));
         if (st != CAST_OK) return st;
         CAST_CUDA(cudaMemsetAsync(sv->partials.ptr, 0, sizeof(double), sv->stream));
         return CAST_OK;
     }
-    cast_status st = ensure_dev(sv, sv->partials, (slots * B + kResultSlots) * sizeof(double));
+    cast_status st = ensure_dev(sv, sv->partials, (need + kResultSlots) * sizeof(double));
     if (st != CAST_OK) return st;
     double *part = reinterpret_cast<double *>(sv->partials.ptr) + kResultSlots;
     size_t used = 0;

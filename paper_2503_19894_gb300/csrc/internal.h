@@ -188,6 +188,9 @@ cast_status launch_pauli_group(const cast_sv *sv, uint64_t x_mask, int n_terms,
                                const double *coeffs, const uint64_t *z_masks, double *d_out,
                                int *n_partials);
 int reduce_grid_blocks();
+// Partial sums launch_pauli_group writes for all groups of G: one launch per
+// kMaxTerms terms of a group, reduce_grid_blocks() partials per launch.
+size_t pauli_partials_needed(const PauliGroups &G);
 int sm_count_cached();
 cast_status launch_set_one(cast_sv *sv, uint64_t index);
 cast_status launch_param_sum(cudaStream_t st, const double *gate_vals, const int *gate_pidx, int ngates,

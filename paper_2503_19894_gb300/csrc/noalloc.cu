@@ -7,6 +7,9 @@
 // must not pass the symbol itself to a kernel (on the host it names a
 // host-side stand-in); the device address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call there.
+// That cached address belongs to the device's primary context: after
+// cudaDeviceReset it is stale, and the call must not be used again in the
+// process.
 //
 // Every call on a device shares the array.  Each call writes every partial
 // sum it later reads, and the final value, before reading them, so nothing
@@ -57,16 +60,16 @@ extern "C" cast_status cast_expectation_noalloc(const cast_sv *sv, const cast_pa
     if (dev != sv->device) return fail(CAST_ERR_ARG, "make the state's device current before this call");
     const PauliGroups G = group_terms(h);
     const size_t B = (size_t)reduce_grid_blocks();
-    size_t launches = 0;
-    for (size_t g = 0; g < G.xm.size(); g++) launches += (G.c[g].size() + 31) / 32;
-    // slot 0: result; then one partial sum per block of every launch
-    const size_t need = 1 + launches * B;
+    // slot 0: result; then one partial sum per block of every launch, counted
+    // by the same helper that sizes cast_expectation's buffer
+    const size_t partials = pauli_partials_needed(G);
+    const size_t need = 1 + partials;
     if (need > CAST_NOALLOC_SCRATCH_DOUBLES)
         return fail(CAST_ERR_ARG, "Pauli sum needs " + std::to_string(need) + " scratch doubles (" +
-                                      std::to_string(launches) + " launches x " + std::to_string(B) +
+                                      std::to_string(partials / B) + " launches x " + std::to_string(B) +
                                       " blocks + 1); the fixed scratch holds " +
                                       std::to_string(CAST_NOALLOC_SCRATCH_DOUBLES));
-    if (launches == 0) {
+    if (partials == 0) {
         *out = 0.0;
         return CAST_OK;
     }
@@ -79,9 +82,12 @@ extern "C" cast_status cast_expectation_noalloc(const cast_sv *sv, const cast_pa
         st = launch_pauli_group(sv, G.xm[g], (int)G.c[g].size(), G.c[g].data(), G.z[g].data(), part + used, &np);
         if (st != CAST_OK) return st;
         used += (size_t)np;
+        if (used > partials) return fail(CAST_ERR_CUDA, "Pauli launches wrote more partial sums than counted");
     }
     if ((st = launch_finalize(sv->stream, part, (int)used, 1, base)) != CAST_OK) return st;
     CAST_CUDA(cudaMemcpyAsync(out, base, sizeof(double), cudaMemcpyDeviceToHost, sv->stream));
     CAST_CUDA(cudaStreamSynchronize(sv->stream));
-    return CAST_OK;
+    // a bounded wait that gave up in earlier work on this stream makes the
+    // state, and so this value, unreliable: report it as cast_expectation does
+    return take_device_error();
 }

@@ -191,6 +191,12 @@ void fill_group(PauliGroupParams<R> *P, uint64_t xm, int nt, const double *coeff
 
 int reduce_grid_blocks() { return sm_count_cached() * 4; }
 
+size_t pauli_partials_needed(const PauliGroups &G) {
+    size_t launches = 0;
+    for (size_t g = 0; g < G.xm.size(); g++) launches += (G.c[g].size() + kMaxTerms - 1) / kMaxTerms;
+    return launches * size_t(reduce_grid_blocks());
+}
+
 cast_status launch_pauli_group(const cast_sv *sv, uint64_t xm, int nt, const double *coeffs,
                                const uint64_t *zm, double *d_partials, int *n_partials) {
     const uint64_t N = uint64_t(1) << sv->n;
