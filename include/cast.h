@@ -119,6 +119,40 @@ cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double 
 cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 
+/* Sparsity-specialised kernels (Section V-A: generated kernels skip zero
+ * entries and specialise real and unit ones; Section IV-C: the cost of a gate
+ * follows its operation count).  A dense-class gate of k = 3..7 qubits may
+ * run through a per-row list of its non-zero entries, each tagged general
+ * complex (4 multiply-adds), real or imaginary (2), or +-1 / +-i (2
+ * additions); entries within 1e-14 of +-1 or +-i count as exactly that value
+ * (the paper's one tolerance).  Process-wide setting:
+ *   CAST_SPARSE_AUTO (default): complex128 (double-float mode) gates of
+ *     k = 6, 7, and of k = 3..5 with at most 3/4 of the dense operation
+ *     count; complex64 gates of k >= 5 with at most 48 operations per
+ *     amplitude (faster than the tensor cores there), and k = 6, 7 when the
+ *     tensor cores are off;
+ *   CAST_SPARSE_OFF: never;  CAST_SPARSE_ALWAYS: every dense-class gate of
+ *     k = 3..7 (complex128 only in double-float mode).
+ * States need n >= 12.  CAST_ERR_ARG for an unknown mode. */
+#define CAST_SPARSE_AUTO 0
+#define CAST_SPARSE_OFF 1
+#define CAST_SPARSE_ALWAYS 2
+cast_status cast_set_sparse_mode(int mode);
+int cast_get_sparse_mode(void);
+
+/* Measured tensor-pipe peak of the current GPU, in dense TFLOP/s: one CTA per
+ * SM issues 32768 back-to-back tcgen05.mma instructions (M = 128, N = 256,
+ * operands in shared memory, fp32 accumulation in tensor memory) and the best
+ * of three timed launches is kept.  kind: CAST_PEAK_TF32 (kind::tf32) or
+ * CAST_PEAK_BF16 (kind::f16 with bf16 operands).  The paper has no
+ * counterpart: this is the denominator of the tensor-core kernels'
+ * utilisation.  Waits; runs on its own stream; allocates nothing on the
+ * device.  CAST_ERR_ARG for an unknown kind, CAST_ERR_TIMEOUT if the MMAs
+ * did not complete within the bounded wait. */
+#define CAST_PEAK_TF32 0
+#define CAST_PEAK_BF16 1
+cast_status cast_measure_tensor_peak(int kind, double *tflops);
+
 /* Failure-detection test hook.  The next tensor-core gate launch waits on an
  * MMA completion that never comes (its issuing thread skips the MMAs), with
  * the barrier wait bounded to wait_limit polls instead of the default 2^26:
@@ -187,12 +221,18 @@ typedef enum {
 /* Measured cost of one gate per size and class on a state of n_qubits
  * qubits: the GPU counterpart of the paper's CostModel (Section IV-C), which
  * records gate times for varying size and sparsity and launch shapes.
- * class index: 0 identity, 1 diagonal, 2 monomial, 3 dense. */
+ * class index: 0 identity, 1 diagonal, 2 monomial, 3 dense.
+ * The sparse kernel's cost grows with the operation count: a dense-class
+ * gate of k = 3..7 qubits with operation count c is estimated at
+ *   min(ms[k][3], max(sparse_floor_ms[k], sparse_ms_per_op[k] * c))
+ * when both sparse entries of k are measured (> 0), else at ms[k][3]. */
 typedef struct {
     int32_t n_qubits;
     int32_t dtype;                                 /* cast_dtype */
     double ms[CAST_MAX_K + 1][4];                  /* average ms per gate; 0 = not measured */
     int32_t blocks_per_sm[CAST_MAX_K + 1][4];      /* best CUDA-core launch width, 0 = default */
+    double sparse_floor_ms[CAST_MAX_K + 1];        /* sparse kernel, two entries per row */
+    double sparse_ms_per_op[CAST_MAX_K + 1];       /* sparse kernel, dense matrix time / its count */
 } cast_cost_table;
 
 typedef struct {
@@ -214,7 +254,10 @@ typedef struct {
 /* Measure the cost table on a scratch state of n_qubits (allocated and
  * freed here) on cuda_stream: one gate of every size 1..CAST_MAX_K and class
  * (diagonal, monomial, dense), for the CUDA-core kernels at launch widths of
- * 1, 2, 4 and 8 blocks per SM keeping the fastest.  Waits for the results. */
+ * 1, 2, 4 and 8 blocks per SM keeping the fastest; then, for k = 3..7 and
+ * n_qubits >= 12, the sparse kernel on a matrix with two entries per row
+ * (its floor) and on the dense one (its time per operation).  Waits for the
+ * results. */
 cast_status cast_autotune(cast_dtype dt, int n_qubits, void *cuda_stream, cast_cost_table *out);
 
 /* Use a table's launch widths for every later launch in this process (per

@@ -152,6 +152,21 @@ def expectation(psi, terms):
     return total
 
 
+def z_string_partial(chunk, offset, qubits):
+    """The part of <psi|Z_q1 ... Z_qm|psi> carried by the amplitudes
+    psi[offset : offset + len(chunk)]:
+        sum_x |psi_x|^2 prod_q (1 - 2 bit_q(x)),
+    in FP64.  A Z string is diagonal, so the full value is the sum of these
+    parts over any split of the index range: states too large to hold twice
+    on the host are checked a slice at a time (<Z_0> of a 30-qubit state)."""
+    c = np.asarray(chunk).astype(np.complex128)
+    x = np.arange(offset, offset + c.size, dtype=np.int64)
+    sign = np.ones(c.size, dtype=np.float64)
+    for q in qubits:
+        sign *= 1.0 - 2.0 * ((x >> q) & 1)
+    return float(np.sum((c.real * c.real + c.imag * c.imag) * sign))
+
+
 def energy(n, gates, theta, terms):
     return expectation(simulate(n, gates, theta=theta), terms)
 

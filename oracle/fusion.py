@@ -76,9 +76,16 @@ def classify(m, zero_tol):
     return DENSE
 
 
-def table_estimate(ms, k, cls):
+def table_estimate(cost, k, cls, ops=0):
     """A measured gate time in integer nanoseconds (identity costs nothing;
-    a missing entry falls back to the dense entry, then to the largest)."""
+    a missing entry falls back to the dense entry, then to the largest).
+
+    cost is either the table ms[k][class] or a dict holding it under "ms"
+    with the sparse kernel's per-k "sparse_floor_ms" and "sparse_ms_per_op":
+    a dense-class gate of k >= 3 qubits and operation count ops then costs
+    min(ms[k][dense], max(floor[k], per_op[k] * ops)) (the sparse kernel's
+    time grows with the operation count, Section IV-C)."""
+    ms = cost["ms"] if isinstance(cost, dict) else cost
     if cls == IDENTITY:
         return 0
     v = ms[k][cls]
@@ -86,6 +93,10 @@ def table_estimate(ms, k, cls):
         v = ms[k][DENSE]
     if not v > 0:
         v = max(ms[kk][c] for kk in range(1, len(ms)) for c in (1, 2, 3))
+    if isinstance(cost, dict) and cls == DENSE and k >= 3:
+        floor, per_op = cost["sparse_floor_ms"][k], cost["sparse_ms_per_op"][k]
+        if floor > 0 and per_op > 0:
+            v = min(v, max(floor, per_op * ops))
     return int(round(v * 1e6))
 
 
@@ -130,7 +141,7 @@ class Fuser:
         self.op_cap = op_cap
         self.tol = zero_tol
         self.P = amp_ops_per_pass
-        self.cost = cost  # ms[k][class] table, or None for the operation-count model
+        self.cost = cost  # ms[k][class] table (or dict, see table_estimate), or None for the operation-count model
 
     def info(self, block):
         if block.info is None:
@@ -141,7 +152,8 @@ class Fuser:
     def est(self, block):
         k = len(block.qubits)
         if self.cost is not None:
-            return table_estimate(self.cost, k, classify(self.info(block)[0], self.tol))
+            m, ops = self.info(block)
+            return table_estimate(self.cost, k, classify(m, self.tol), ops)
         return max(self.P * 128, self.info(block)[1] << (7 - k))
 
     def fusible(self, top, bot, k):
@@ -227,7 +239,7 @@ def fuse(n, gates, theta=None, mode="adaptive", max_k=5, agglomerative=True, op_
         best, best_plan = None, None
         for k in range(2, 8):
             plan = fuse(n, gates, theta, mode, k, agglomerative, op_cap, zero_tol, amp_ops_per_pass, cost)
-            total = sum(table_estimate(cost, len(q), classify(m, zero_tol)) for q, m, _ in plan)
+            total = sum(table_estimate(cost, len(q), classify(m, zero_tol), ops) for q, m, ops in plan)
             if best is None or total < best:
                 best, best_plan = total, plan
         return best_plan

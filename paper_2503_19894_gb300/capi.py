@@ -44,7 +44,9 @@ class cast_circuit(ctypes.Structure):
 class cast_cost_table(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("ms", (ctypes.c_double * 4) * (CAST_MAX_K + 1)),
-                ("blocks_per_sm", (ctypes.c_int32 * 4) * (CAST_MAX_K + 1))]
+                ("blocks_per_sm", (ctypes.c_int32 * 4) * (CAST_MAX_K + 1)),
+                ("sparse_floor_ms", ctypes.c_double * (CAST_MAX_K + 1)),
+                ("sparse_ms_per_op", ctypes.c_double * (CAST_MAX_K + 1))]
 
 
 class cast_options(ctypes.Structure):
@@ -73,7 +75,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_expectation_noalloc", "cast_set_tensor_mode", "cast_get_tensor_mode",
            "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
            "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table",
-           "cast_debug_inject_timeout")
+           "cast_debug_inject_timeout", "cast_measure_tensor_peak", "cast_set_sparse_mode",
+           "cast_get_sparse_mode")
 
 _lib = None
 
@@ -130,6 +133,9 @@ def load(build_if_missing=True):
         "cast_autotune": (I, [I, I, P, P]),
         "cast_set_cost_table": (I, [P]),
         "cast_debug_inject_timeout": (I, [ctypes.c_uint32]),
+        "cast_measure_tensor_peak": (I, [I, P]),
+        "cast_set_sparse_mode": (I, [I]),
+        "cast_get_sparse_mode": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -262,16 +268,26 @@ def options(fusion="adaptive", max_k=5, agglomerative=True, op_cap=4096, zero_to
     return o
 
 
-def cost_table(ms, dtype="c64", n_qubits=0, blocks_per_sm=None):
+def cost_table(ms, dtype="c64", n_qubits=0, blocks_per_sm=None, sparse_floor_ms=None, sparse_ms_per_op=None):
     """A cast_cost_table from nested lists ms[k][class] (k = 0..7; class 0
-    identity, 1 diagonal, 2 monomial, 3 dense)."""
+    identity, 1 diagonal, 2 monomial, 3 dense) and, optionally, the sparse
+    kernel's per-k floor and time per operation."""
     t = cast_cost_table()
     t.n_qubits, t.dtype = n_qubits, _dt(dtype)
     for k in range(CAST_MAX_K + 1):
         for c in range(4):
             t.ms[k][c] = float(ms[k][c])
             t.blocks_per_sm[k][c] = int(blocks_per_sm[k][c]) if blocks_per_sm is not None else 0
+        t.sparse_floor_ms[k] = float(sparse_floor_ms[k]) if sparse_floor_ms is not None else 0.0
+        t.sparse_ms_per_op[k] = float(sparse_ms_per_op[k]) if sparse_ms_per_op is not None else 0.0
     return t
+
+
+def cost_table_dict(t):
+    """The table as plain lists (the form oracle.fusion takes)."""
+    return {"ms": [[t.ms[k][c] for c in range(4)] for k in range(CAST_MAX_K + 1)],
+            "sparse_floor_ms": [t.sparse_floor_ms[k] for k in range(CAST_MAX_K + 1)],
+            "sparse_ms_per_op": [t.sparse_ms_per_op[k] for k in range(CAST_MAX_K + 1)]}
 
 
 def cast_autotune(dtype, n_qubits, stream=0):
@@ -441,6 +457,25 @@ def cast_set_tensor_mode(mode):
 
 def cast_get_tensor_mode():
     return int(load().cast_get_tensor_mode())
+
+
+CAST_PEAK_TF32, CAST_PEAK_BF16 = 0, 1
+CAST_SPARSE_AUTO, CAST_SPARSE_OFF, CAST_SPARSE_ALWAYS = 0, 1, 2
+
+
+def cast_set_sparse_mode(mode):
+    _check(load().cast_set_sparse_mode(int(mode)))
+
+
+def cast_get_sparse_mode():
+    return int(load().cast_get_sparse_mode())
+
+
+def cast_measure_tensor_peak(kind=CAST_PEAK_TF32):
+    """Measured dense tensor-pipe TFLOP/s of the current GPU (kind::tf32 or bf16)."""
+    v = ctypes.c_double()
+    _check(load().cast_measure_tensor_peak(int(kind), ctypes.byref(v)))
+    return float(v.value)
 
 
 # --------------------------------------------- batched hardware-efficient ansatz

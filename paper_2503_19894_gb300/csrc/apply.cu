@@ -497,6 +497,7 @@ int sm_count_cached() {
 }
 
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g) {
+    if (sparse_preferred(sv, g)) return launch_gate_sparse(sv, g);
     if (tcc_eligible(sv, g)) return launch_gate_tcc(sv, g);
     if (tc_eligible(sv, g)) return launch_gate_tc(sv, g);
     if (df_eligible(sv, g)) return launch_gate_df(sv, g);

@@ -25,6 +25,34 @@ std::vector<cplx> sample_matrix(int k, int cls) {
         }
     return m;
 }
+// unitary with two entries per row: H on local bit 0, identity elsewhere
+std::vector<cplx> two_per_row_matrix(int k) {
+    const int d = 1 << k;
+    std::vector<cplx> m(size_t(d) * d, cplx(0.0, 0.0));
+    const double h = 1.0 / std::sqrt(2.0);
+    for (int r = 0; r < d; r++) {
+        m[size_t(r) * d + (r & ~1)] = cplx(h, 0.0);
+        m[size_t(r) * d + (r | 1)] = cplx((r & 1) ? -h : h, 0.0);
+    }
+    return m;
+}
+
+// average ms of one launch of g (two warm-up launches, three timed)
+cast_status time_gate(cast_sv *sv, const PreparedGate &g, cudaEvent_t e0, cudaEvent_t e1, double *per) {
+    cast_status st = CAST_OK;
+    for (int rep = 0; rep < 2 && st == CAST_OK; rep++) st = launch_gate(sv, g);
+    if (st != CAST_OK) return st;
+    cudaEventRecord(e0, sv->stream);
+    const int reps = 3;
+    for (int rep = 0; rep < reps && st == CAST_OK; rep++) st = launch_gate(sv, g);
+    cudaEventRecord(e1, sv->stream);
+    if (st != CAST_OK) return st;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune timing");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *per = double(ms) / reps;
+    return CAST_OK;
+}
 }  // namespace
 
 int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def) {
@@ -36,12 +64,16 @@ int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def) {
 }
 
 // cost-table estimate of a block (integer nanoseconds), used by the fusion pass
-int64_t table_estimate(const cast_cost_table &t, int k, int cls) {
+int64_t table_estimate(const cast_cost_table &t, int k, int cls, int64_t ops) {
     double ms = t.ms[k][cls];
     if (cls != CLS_IDENTITY && !(ms > 0)) ms = t.ms[k][CLS_DENSE];
     if (cls != CLS_IDENTITY && !(ms > 0)) {
         for (int kk = 1; kk <= CAST_MAX_K; kk++)
             for (int c = 1; c < 4; c++) ms = std::max(ms, t.ms[kk][c]);
+    }
+    if (cls == CLS_DENSE && k >= 3 && t.sparse_floor_ms[k] > 0 && t.sparse_ms_per_op[k] > 0) {
+        const double sp = std::max(t.sparse_floor_ms[k], t.sparse_ms_per_op[k] * double(ops));
+        ms = std::min(ms, sp);
     }
     return cls == CLS_IDENTITY ? 0 : int64_t(std::llround(ms * 1e6));
 }
@@ -124,6 +156,25 @@ cast_status cast_autotune(cast_dtype dt, int n, void *stream, cast_cost_table *o
             out->blocks_per_sm[k][cls] = best_w;
         }
     }
+    // the sparse kernel (k = 3..7): its floor with two entries per row, and
+    // its time per operation with the dense sample
+    const int sparse_saved = cast_get_sparse_mode();
+    if (n >= 12) cast_set_sparse_mode(CAST_SPARSE_ALWAYS);
+    for (int k = 3; k <= CAST_MAX_K && st == CAST_OK && n >= 12; k++) {
+        int qs[CAST_MAX_K];
+        for (int i = 0; i < k; i++) qs[i] = int(std::lround(double(i) * (n - 1) / (k - 1)));
+        for (int which = 0; which < 2 && st == CAST_OK; which++) {
+            std::vector<cplx> m = which == 0 ? two_per_row_matrix(k) : sample_matrix(k, CLS_DENSE);
+            PreparedGate g;
+            if ((st = prepare_gate(n, qs, k, m.data(), 1e-12, &g)) != CAST_OK) break;
+            if (!sparse_preferred(sv, g)) break;  // e.g. complex128 in native FP64 mode
+            double per = 0;
+            if ((st = time_gate(sv, g, e0, e1, &per)) != CAST_OK) break;
+            if (which == 0) out->sparse_floor_ms[k] = per;
+            else out->sparse_ms_per_op[k] = per / double(opcount(g.m.data(), k, 0.0));
+        }
+    }
+    cast_set_sparse_mode(sparse_saved);
     {  // leave the process-wide table as it was before the call
         std::lock_guard<std::mutex> lk(g_mu);
         g_tab[ti] = saved_tab;

@@ -111,7 +111,7 @@ struct Fuser {
 
     int64_t cost(const Block &b) const {
         const int k = (int)b.q.size();
-        if (opt.cost) return table_estimate(*opt.cost, k, classify_matrix(b.m.data(), k, opt.zero_tol));
+        if (opt.cost) return table_estimate(*opt.cost, k, classify_matrix(b.m.data(), k, opt.zero_tol), b.ops);
         const int64_t mem = P * 128;
         const int64_t cmp = b.ops << (7 - k);
         return mem > cmp ? mem : cmp;
@@ -257,7 +257,8 @@ cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast
         cast_status st = fuse_once(c, params, &o, &cand);
         if (st != CAST_OK) return st;
         int64_t total = 0;
-        for (const FusedGate &g : cand) total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol));
+        for (const FusedGate &g : cand)
+            total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol), g.ops);
         if (best < 0 || total < best) {
             best = total;
             out->swap(cand);

@@ -128,9 +128,10 @@ cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast
                          std::vector<FusedGate> *out);
 
 // --------------------------------------------------------------- kernels
-// Matrix ring: kMatSlots slots of kMatSlotBytes (a 7-qubit complex128 matrix).
+// Matrix ring: kMatSlots slots of kMatSlotBytes (a 7-qubit complex128 matrix, or
+// the entry list of a dense 7-qubit complex128 gate for the sparse kernel).
 constexpr int kMatSlots = 16;
-constexpr size_t kMatSlotBytes = size_t(16) << 14;
+constexpr size_t kMatSlotBytes = size_t(512) << 10;
 // Copy `bytes` (<= kMatSlotBytes) of host data to a device slot, in stream
 // order on sv's stream; *dev receives the slot's device address.
 cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const void **dev);
@@ -171,10 +172,16 @@ bool tensor_mode_tf32x3();          // cast_set_tensor_mode(CAST_TC_TF32X3) in e
 uint32_t take_inject_limit();       // cast_debug_inject_timeout's pending limit, cleared (0: none)
 // Autotuned launch width (blocks per SM) of a CUDA-core kernel, or def.
 int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def);
-// Cost-table estimate of one gate of size k and class cls, in integer ns.
-int64_t table_estimate(const cast_cost_table &t, int k, int cls);
+// Cost-table estimate of one gate of size k, class cls and operation count
+// ops, in integer ns.
+int64_t table_estimate(const cast_cost_table &t, int k, int cls, int64_t ops);
 // Class of a 2^k x 2^k matrix (identity / diagonal / monomial / dense).
 int classify_matrix(const cplx *m, int k, double zero_tol);
+
+// Sparsity-specialised kernels (apply_sparse.cu): per-row entry lists, k = 3..7.
+bool sparse_preferred(const cast_sv *sv, const PreparedGate &g);
+cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g);
+int64_t dense_opcount(int k);
 
 // Double-float path for complex128 gates (apply_df.cu).
 bool df_eligible(const cast_sv *sv, const PreparedGate &g);

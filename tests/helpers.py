@@ -32,3 +32,16 @@ def sorted_gate(qubits, m):
     d = 1 << k
     old = np.array([sum(((j >> i) & 1) << order[i] for i in range(k)) for j in range(d)])
     return tuple(sorted(qubits)), np.asarray(m)[old[:, None], old[None, :]]
+
+
+def rel_err(got, ref):
+    """||got - ref||_2 / ||ref||_2: the error relative to the state's size,
+    which stays meaningful when amplitudes are small (large n)."""
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+# Relative error bounds beside the absolute ones (complex128 1e-12, complex64
+# 1e-5): complex128 results stay at the FP64 / double-float level, complex64
+# results at a few FP32 units in the last place per gate, accumulated as a
+# random walk over the circuit.
+REL = {"c128": 1e-12, "c64": 2e-5}

@@ -98,3 +98,30 @@ def test_cost_table_fusion_matches_oracle(name, n, make, max_k):
 def test_max_k_zero_needs_a_cost_table():
     with pytest.raises(capi.CastError):
         capi.cast_fuse(4, W.random_circuit(4, 2, 0), opts=capi.options("adaptive", 0))
+
+
+SPARSE_FLOOR = [0, 0, 0, 0.17, 0.18, 0.2, 0.22, 0.25]
+SPARSE_PER_OP = [0, 0, 0, 2e-4, 1e-4, 6e-5, 3e-5, 2e-5]
+
+
+@pytest.mark.parametrize("name,n,make", CASES)
+@pytest.mark.parametrize("max_k", [5, 7, 0])
+def test_sparse_cost_table_fusion_matches_oracle(name, n, make, max_k):
+    gates = make()
+    theta = W.uniform_params(2 * n * 3, -3, 3, 0) if name.startswith("hea") else None
+    table = capi.cost_table(SAMPLE_MS, sparse_floor_ms=SPARSE_FLOOR, sparse_ms_per_op=SPARSE_PER_OP)
+    got = capi.cast_fuse(n, gates, theta, opts=capi.options("adaptive", max_k, cost=table))
+    ref = ofu.fuse(n, gates, theta, mode="adaptive", max_k=max_k, cost=capi.cost_table_dict(table))
+    assert [q for q, _, _ in got] == [q for q, _, _ in ref]
+    for (_, a, _), (_, b, _) in zip(got, ref):
+        assert np.max(np.abs(a - b)) < 1e-12
+
+
+@pytest.mark.parametrize("fam", sorted(W.FAMILIES))
+def test_family_plans_match_oracle(fam):
+    """The six benchmark families (20 qubits): size-only and adaptive fusion,
+    the same blocks and operation counts as the reference."""
+    n = 20
+    gates = W.benchmark_family(fam, n, seed=4)[:500]
+    for mode in ("size", "adaptive"):
+        _compare(n, gates, None, fusion=mode, max_k=5, agglomerative=True, amp_ops_per_pass=16)

@@ -210,6 +210,37 @@ def test_table_estimate_lookup_and_fallbacks():
     assert ofu.table_estimate(ms, 3, ofu.DENSE) == 300000
 
 
+def test_table_estimate_sparse_terms():
+    """min(dense, max(floor, per_op * ops)) for dense-class gates of k >= 3;
+    other classes and k < 3 ignore the sparse terms."""
+    ms = [[0, 0, 0, 0]] + [[0, 0.1, 0.12, 0.5]] * 7
+    cost = {"ms": ms, "sparse_floor_ms": [0, 0, 0, 0.2, 0.2, 0.2, 0.2, 0.2],
+            "sparse_ms_per_op": [0, 0, 0, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4]}
+    assert ofu.table_estimate(cost, 5, ofu.DENSE, 1000) == 200000    # floor 0.2 > 0.1
+    assert ofu.table_estimate(cost, 5, ofu.DENSE, 4096) == 409600    # 0.4096 < 0.5
+    assert ofu.table_estimate(cost, 5, ofu.DENSE, 8000) == 500000    # the dense kernel, 0.5
+    assert ofu.table_estimate(cost, 2, ofu.DENSE, 10) == 500000      # k < 3: no sparse kernel
+    assert ofu.table_estimate(cost, 5, ofu.DIAGONAL, 10) == 100000
+    assert ofu.table_estimate(ms, 5, ofu.DENSE, 10) == 500000        # plain table: no sparse terms
+
+
+def test_sparse_cost_lets_a_sparse_merge_through():
+    """CX(0,1), CX(1,2) then H(2).  At size 2, CX(1,2) and H(2) fuse (a
+    dense-class 2-qubit block, 0.3 ms <= 0.12 + 0.3).  At size 3 that block
+    and CX(0,1) (0.12) would make a dense-class 3-qubit block of 32
+    operations: with the sparse terms it costs max(0.2, 1e-4 * 32) = 0.2 ms
+    <= 0.42 and fuses; with the plain table it costs the dense 0.5 ms > 0.42
+    and is refused."""
+    ms = [[0, 0, 0, 0]] + [[0, 0.1, 0.12, 0.3]] * 2 + [[0, 0.1, 0.12, 0.5]] * 5
+    cost = {"ms": ms, "sparse_floor_ms": [0, 0, 0, 0.2, 0.2, 0.2, 0.2, 0.2],
+            "sparse_ms_per_op": [0, 0, 0, 1e-4, 1e-4, 1e-4, 1e-4, 1e-4]}
+    gates = [W.Gate("CX", (0, 1)), W.Gate("CX", (1, 2)), W.Gate("H", (2,))]
+    with_sparse = _fused_qubits(gates, mode="adaptive", max_k=3, cost=cost)
+    without = _fused_qubits(gates, mode="adaptive", max_k=3, cost=ms)
+    assert with_sparse == [(0, 1, 2)]
+    assert without != [(0, 1, 2)]
+
+
 def test_cost_table_decisions():
     """With measured costs: two diagonal 2-qubit gates fuse into a diagonal
     3-qubit gate when cost(3, diag) <= 2 cost(2, diag) and not otherwise;

@@ -109,30 +109,6 @@ def test_hea_matches_single_state_adjoint(f64):
     capi.cast_hea_destroy(b)
 
 
-@with_modes(1e-10, 2e-4)
-def test_hea_wide_groups_match_single_state_adjoint(dtype, f64, tol):
-    """Instances whose later groups rotate 3..7 qubits (bits held in registers
-    and the fixed shared-memory rounds) against cast_adjoint_grad, the per-gate
-    adjoint checked against parameter shift elsewhere, in the same precision."""
-    import paper_2503_19894_gb300 as pkg
-    ns, layers, zz, hx = [19, 20, 17], 2, 1.0, 0.7
-    b = capi.cast_hea_create(ns, layers, dtype, with_grad=True)
-    npar, _ = capi.cast_hea_info(b)
-    theta = W.uniform_params(npar, -math.pi, math.pi, 21)
-    e, g = capi.cast_hea_grad(b, theta, zz, hx, len(ns))
-    for n, th, ei, gi in zip(ns, split(theta, ns, layers), e, split(g, ns, layers)):
-        gates, _ = W.hea_ansatz(n, layers)
-        H = tfim(n, zz, hx)
-        psi = pkg.StateVector(n, "c128")
-        lam = pkg.StateVector(n, "c128", init_index=None)
-        e1, g1 = pkg.cast_adjoint_grad(psi.handle, lam.handle, n, gates, th, H)
-        psi.close()
-        lam.close()
-        assert abs(ei - e1) <= tol * n, (n, ei, e1)
-        assert np.max(np.abs(gi - g1)) <= tol * n, (n, np.max(np.abs(gi - g1)))
-    capi.cast_hea_destroy(b)
-
-
 def test_hea_arguments_rejected():
     with pytest.raises(capi.CastError):
         capi.cast_hea_create([1], 2, "c64")

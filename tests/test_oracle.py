@@ -216,6 +216,25 @@ def test_tfim_special_states(n, hx):
     assert abs(oracle.expectation(plus, H) - hx * n) < 1e-13
 
 
+def test_z_string_partial_sums_to_expectation():
+    """Split over three index ranges, the parts add up to <psi|Z..Z|psi> of the
+    Pauli-string expectation (which applies Z factors as gates), and <Z_0>
+    after H(0) on |0..0> is 0 while <Z_0> of |0..0> is 1."""
+    n = 9
+    psi = W.random_state(n, 4)
+    for qs in ((0,), (3,), (0, 8), (1, 2, 7)):
+        want = oracle.expectation(psi, [W.PauliTerm(1.0, "Z" * len(qs), qs)])
+        cuts = [0, 100, 301, 1 << n]
+        got = sum(oracle.z_string_partial(psi[a:b], a, qs) for a, b in zip(cuts[:-1], cuts[1:]))
+        assert abs(got - want) < 1e-14
+    plus = oracle.simulate(n, [W.Gate("H", (0,))])
+    assert abs(oracle.z_string_partial(plus, 0, (0,))) < 1e-15
+    assert oracle.z_string_partial(oracle.basis_state(n), 0, (0,)) == 1.0
+    # a planted sign error (bit q counted as +1) is caught
+    odd = oracle.basis_state(n, 1)
+    assert oracle.z_string_partial(odd, 0, (0,)) == -1.0
+
+
 def test_y_expectation_sign():
     # S H |0> = (|0> + i|1>)/sqrt2 is the +1 eigenstate of Y
     psi = oracle.simulate(1, [W.Gate("H", (0,)), W.Gate("S", (0,))])

@@ -18,6 +18,22 @@ exact instances are not published, so seeded stand-ins are generated here:
   hea_ansatz       hardware-efficient ansatz: RY on all, RZ on all, CZ ladder
   tfim_hamiltonian sum Z_i Z_{i+1} + h sum X_i (open boundary)
   vqa_batch        many ansatz instances of uneven qubit counts
+  ala_circuit      alternating layered ansatz: U3 on every qubit, then CZ on
+                   the even or odd neighbour pairs, alternating by layer
+  qvc_circuit      quantum-volume-shaped circuit: per layer a random pairing,
+                   each pair a random two-qubit block of the generic
+                   three-CX shape (four U3 layers around three CX)
+  iqp_circuit      instantaneous quantum polynomial: H on all, diagonal
+                   rounds (RZ on all, CP on a random matching), H on all
+  hes_circuit      first-order Trotter steps of the 1-D Heisenberg chain
+                   sum (XX + YY + ZZ) + h sum Z, each bond term as basis
+                   change + CX + RZ + CX
+  benchmark_family one of the six families of the paper by name
+
+The paper names the six families (QFT, ALA, RQC, QVC, IQP, HES) and splits
+them into a sparse class (QFT, RQC, IQP, HES) and a dense class (ALA, QVC,
+mostly dense single-qubit gates) but gives no instance; the shapes above are
+the cited constructions written as gate lists.
 """
 import math
 from typing import NamedTuple, Optional
@@ -193,3 +209,115 @@ def random_state_device(n, dtype, seed):
     del re, im
     psi /= torch.linalg.vector_norm(psi)
     return psi
+
+
+def _u3_angles(rng, count):
+    return rng.uniform(0.0, 2.0 * math.pi, size=(count, 3))
+
+
+def ala_circuit(n, layers, seed):
+    """Alternating layered ansatz (Cerezo et al. 2021, the ALA family): layer
+    l applies U3(theta, phi, lambda) with angles U(0, 2 pi) to every qubit,
+    then CZ(i, i+1) for every i with i = l (mod 2), i + 1 < n: two-qubit
+    blocks in a brick pattern whose offset alternates between layers."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for l in range(layers):
+        ang = _u3_angles(rng, n)
+        for q in range(n):
+            gates.append(Gate("U3", (q,), tuple(float(a) for a in ang[q])))
+        for i in range(l % 2, n - 1, 2):
+            gates.append(Gate("CZ", (i, i + 1)))
+    return gates
+
+
+def qvc_circuit(n, layers, seed):
+    """Quantum-volume-shaped circuit (Cross et al. 2019, the QVC family): per
+    layer a random permutation p pairs the qubits (p[2i], p[2i+1]); each pair
+    gets a random two-qubit block of the generic shape
+        U3 x U3, CX(a, b), U3 x U3, CX(b, a), U3 x U3, CX(a, b), U3 x U3
+    with U3 angles U(0, 2 pi) (random blocks of the three-CX form rather than
+    Haar-distributed SU(4), so the circuit is mostly dense 1-qubit gates)."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(layers):
+        perm = rng.permutation(n)
+        for i in range(n // 2):
+            a, b = int(perm[2 * i]), int(perm[2 * i + 1])
+            ang = _u3_angles(rng, 8)
+            for r in range(4):
+                gates.append(Gate("U3", (a,), tuple(float(v) for v in ang[2 * r])))
+                gates.append(Gate("U3", (b,), tuple(float(v) for v in ang[2 * r + 1])))
+                if r < 3:
+                    gates.append(Gate("CX", (a, b) if r != 1 else (b, a)))
+    return gates
+
+
+def iqp_circuit(n, layers, seed, zero_phases=False):
+    """Instantaneous quantum polynomial circuit (Bremner, Montanaro and
+    Shepherd 2017, the IQP family): H on every qubit, then `layers` diagonal
+    rounds, each RZ(theta) on every qubit and CP(phi) on a random perfect
+    matching (angles U(0, 2 pi)), then H on every qubit.  With zero_phases
+    every angle is 0 and the circuit is the identity."""
+    rng = np.random.default_rng(seed)
+    gates = [Gate("H", (q,)) for q in range(n)]
+    for _ in range(layers):
+        th = rng.uniform(0.0, 2.0 * math.pi, size=n)
+        for q in range(n):
+            gates.append(Gate("RZ", (q,), (0.0 if zero_phases else float(th[q]),)))
+        perm = rng.permutation(n)
+        ph = rng.uniform(0.0, 2.0 * math.pi, size=n // 2)
+        for i in range(n // 2):
+            gates.append(Gate("CP", (int(perm[2 * i]), int(perm[2 * i + 1])), (0.0 if zero_phases else float(ph[i]),)))
+    gates += [Gate("H", (q,)) for q in range(n)]
+    return gates
+
+
+def hes_bond(a, b, pauli, angle):
+    """exp(-i (angle / 2) P_a P_b) for P in {X, Y, Z} as a gate list: a basis
+    change to Z (H for X; RX(pi/2) for Y), CX(a, b), RZ(angle) on b, CX(a, b),
+    and the basis change undone."""
+    pre, post = [], []
+    if pauli == "X":
+        pre = [Gate("H", (a,)), Gate("H", (b,))]
+        post = list(pre)
+    elif pauli == "Y":
+        pre = [Gate("RX", (a,), (math.pi / 2,)), Gate("RX", (b,), (math.pi / 2,))]
+        post = [Gate("RX", (a,), (-math.pi / 2,)), Gate("RX", (b,), (-math.pi / 2,))]
+    core = [Gate("CX", (a, b)), Gate("RZ", (b,), (float(angle),)), Gate("CX", (a, b))]
+    return pre + core + post
+
+
+def hes_circuit(n, steps, dt=0.1, field=0.5, paulis="XYZ"):
+    """Hamiltonian evolution simulation (Low and Chuang 2017, the HES family)
+    as first-order Trotter steps of the open 1-D Heisenberg chain
+        H = sum_i (X_i X_{i+1} + Y_i Y_{i+1} + Z_i Z_{i+1}) + field sum_i Z_i:
+    per step, for every bond (i, i+1) and P in `paulis`, exp(-i dt P_i P_{i+1})
+    (hes_bond with angle 2 dt), then RZ(2 dt field) on every qubit, i.e.
+    exp(-i dt field Z_i).  The initial state is the caller's."""
+    gates = []
+    for _ in range(steps):
+        for i in range(n - 1):
+            for p in paulis:
+                gates += hes_bond(i, i + 1, p, 2.0 * dt)
+        if field:
+            gates += [Gate("RZ", (q,), (2.0 * dt * field,)) for q in range(n)]
+    return gates
+
+
+# name -> (generator(n, seed), class): the six benchmark families at the
+# sizes the fusion ablation runs (layers chosen so every family has a few
+# hundred to two thousand gates at 30 qubits)
+FAMILIES = {
+    "QFT": (lambda n, seed: qft_circuit(n), "sparse"),
+    "RQC": (lambda n, seed: random_circuit(n, 30, seed), "sparse"),
+    "IQP": (lambda n, seed: iqp_circuit(n, 10, seed), "sparse"),
+    "HES": (lambda n, seed: hes_circuit(n, 2), "sparse"),
+    "ALA": (lambda n, seed: ala_circuit(n, 10, seed), "dense"),
+    "QVC": (lambda n, seed: qvc_circuit(n, 10, seed), "dense"),
+}
+
+
+def benchmark_family(name, n, seed=1):
+    """Gate list of one of the paper's six benchmark families."""
+    return FAMILIES[name][0](n, seed)
