@@ -119,6 +119,25 @@ cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double 
 cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 
+/* complex128 dense gates on the tensor cores (process-wide setting):
+ *   CAST_C128_TC_OFF (default): double-float arithmetic on the FP32 pipe;
+ *   CAST_C128_TC_OZAKI: dense gates of k = 3..5 on states of n >= k + 7
+ *     qubits (in CAST_F64_EMULATED mode) as exact products of 7-bit digits
+ *     on tcgen05 (kind::f16, bf16 operands, fp32 accumulation that never
+ *     rounds for the three leading digit sums): each slice row and each row
+ *     of the gate's real form is scaled by a power of two and cut to 49
+ *     fractional bits, the digit-pair products with i + j <= 6 are
+ *     accumulated by weight, and the result is assembled with integer
+ *     operations; error ~2^-45 of the slice's largest amplitude.  Gates with
+ *     at most a quarter of the dense operation count stay on the sparse
+ *     kernel.  The paper has no tensor-core path; this is the complex128
+ *     form of Eq. 3's matvec on GB300's tensor cores.
+ * CAST_ERR_ARG for an unknown mode. */
+#define CAST_C128_TC_OFF 0
+#define CAST_C128_TC_OZAKI 1
+cast_status cast_set_c128_tensor_mode(int mode);
+int cast_get_c128_tensor_mode(void);
+
 /* Sparsity-specialised kernels (Section V-A: generated kernels skip zero
  * entries and specialise real and unit ones; Section IV-C: the cost of a gate
  * follows its operation count).  A dense-class gate of k = 3..7 qubits may
@@ -127,10 +146,10 @@ int cast_get_tensor_mode(void);
  * additions); entries within 1e-14 of +-1 or +-i count as exactly that value
  * (the paper's one tolerance).  Process-wide setting:
  *   CAST_SPARSE_AUTO (default): complex128 (double-float mode) gates of
- *     k = 6, 7, and of k = 3..5 with at most 3/4 of the dense operation
- *     count; complex64 gates of k >= 5 with at most 48 operations per
- *     amplitude (faster than the tensor cores there), and k = 6, 7 when the
- *     tensor cores are off;
+ *     k = 4, 6, 7, and of k = 3, 5 with at most 3/4 of the dense operation
+ *     count; complex64 dense-class gates that the tensor cores do not take
+ *     (non-unitary, or tensor cores off) of k >= 5, and of k = 4 with at
+ *     most 24 operations per amplitude;
  *   CAST_SPARSE_OFF: never;  CAST_SPARSE_ALWAYS: every dense-class gate of
  *     k = 3..7 (complex128 only in double-float mode).
  * States need n >= 12.  CAST_ERR_ARG for an unknown mode. */

@@ -76,7 +76,7 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
            "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table",
            "cast_debug_inject_timeout", "cast_measure_tensor_peak", "cast_set_sparse_mode",
-           "cast_get_sparse_mode")
+           "cast_get_sparse_mode", "cast_set_c128_tensor_mode", "cast_get_c128_tensor_mode")
 
 _lib = None
 
@@ -136,6 +136,8 @@ def load(build_if_missing=True):
         "cast_measure_tensor_peak": (I, [I, P]),
         "cast_set_sparse_mode": (I, [I]),
         "cast_get_sparse_mode": (I, []),
+        "cast_set_c128_tensor_mode": (I, [I]),
+        "cast_get_c128_tensor_mode": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -469,6 +471,17 @@ def cast_set_sparse_mode(mode):
 
 def cast_get_sparse_mode():
     return int(load().cast_get_sparse_mode())
+
+
+CAST_C128_TC_OFF, CAST_C128_TC_OZAKI = 0, 1
+
+
+def cast_set_c128_tensor_mode(mode):
+    _check(load().cast_set_c128_tensor_mode(int(mode)))
+
+
+def cast_get_c128_tensor_mode():
+    return int(load().cast_get_c128_tensor_mode())
 
 
 def cast_measure_tensor_peak(kind=CAST_PEAK_TF32):

@@ -288,6 +288,61 @@ k_diag(typename Cx<R>::T *__restrict__ sv, uint64_t N, Targets tg,
     }
 }
 
+// Chunked form for states of at least 2^12 amplitudes: a CTA iteration
+// covers a contiguous chunk of 256 x UNR 16-byte vectors (thread t takes
+// vectors t, t + 256, ...: coalesced).  The diagonal index of an amplitude is
+// the OR of three parts formed once: the chunk's (targets above the chunk),
+// the thread's (its lane's address bits within a round) and the round's, plus
+// the amplitude's own bit 0 when qubit 0 is a target; the per-amplitude
+// bit-by-bit extraction of k_diag is gone.
+// The round parts jr[u] and the bit-0 part j0 are the same for every thread
+// and come with the launch parameters.
+struct DiagChunkBits {
+    int jr[8];
+    int j0;
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(256)
+k_diag_chunk(typename Cx<R>::T *__restrict__ sv, uint64_t nchunks, const __grid_constant__ Targets tg,
+             const __grid_constant__ DiagVec<R, K> D, const __grid_constant__ DiagChunkBits cb) {
+    using V = typename Vec16<R>::T;
+    constexpr int A = Vec16<R>::A, LA = A == 2 ? 1 : 0, UNR = 8, CB = 8 + 3 + LA;
+    auto jbits = [&](uint64_t x) {
+        int j = 0;
+#pragma unroll
+        for (int b = 0; b < K; b++) j |= int((x >> tg.q[b]) & 1) << b;
+        return j;
+    };
+    const int jt = jbits(uint64_t(threadIdx.x) << LA);
+    const int j0 = cb.j0;
+    V *vp = reinterpret_cast<V *>(sv);
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint64_t base = c << CB;
+        const int jh = jbits(base) | jt;
+        V *p = vp + (base >> LA) + threadIdx.x;
+        uint32_t act = 0;
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const int jj = jh | cb.jr[u];
+            const bool a = K > 5 || !((D.skip >> jj) & 1) || (A == 2 && !((D.skip >> (jj | j0)) & 1));
+            act |= uint32_t(a) << u;
+        }
+        V v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++)
+            if ((act >> u) & 1) v[u] = p[256 * u];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (!((act >> u) & 1)) continue;
+            const int jj = jh | cb.jr[u];
+            vec_set<R>(v[u], 0, cmul(D.d[jj], vec_amp<R>(v[u], 0)));
+            if (A == 2) vec_set<R>(v[u], 1, cmul(D.d[jj | j0], vec_amp<R>(v[u], 1)));
+            p[256 * u] = v[u];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- monomial
 template <typename R, int K>
 struct MonoVec {
@@ -412,8 +467,21 @@ cast_status run_diag(cast_sv *sv, const PreparedGate &g, const Targets &tg) {
     const double frac = double(touched) / double(1 << K);
     ProfScope ps(sv->stream, "diag_k" + std::to_string(K) + "_" + dt_name(sv->dt),
                  2.0 * double(sizeof(T2)) * double(N) * frac, 6.0 * double(N) * frac);
-    k_diag<R, K><<<(unsigned)grid_for(N, tuned_blocks_per_sm(sv->dt, K, CLS_DIAG, 8)), 256, 0, sv->stream>>>(
-        reinterpret_cast<T2 *>(sv->data), N, tg, D);
+    if (sv->n >= 12) {
+        constexpr int LA = sizeof(R) == 4 ? 1 : 0, CB = 8 + 3 + LA;
+        DiagChunkBits cb{};
+        for (int u = 0; u < 8; u++)
+            for (int b = 0; b < K; b++) cb.jr[u] |= int(((uint64_t(u) << (8 + LA)) >> g.q[b]) & 1) << b;
+        for (int b = 0; b < K; b++)
+            if (LA == 1 && g.q[b] == 0) cb.j0 = 1 << b;
+        const uint64_t nchunks = N >> CB;
+        const uint64_t cap = uint64_t(sm_count_cached()) * tuned_blocks_per_sm(sv->dt, K, CLS_DIAG, 8);
+        k_diag_chunk<R, K><<<(unsigned)(nchunks < cap ? nchunks : cap), 256, 0, sv->stream>>>(
+            reinterpret_cast<T2 *>(sv->data), nchunks, tg, D, cb);
+    } else {
+        k_diag<R, K><<<(unsigned)grid_for(N, tuned_blocks_per_sm(sv->dt, K, CLS_DIAG, 8)), 256, 0, sv->stream>>>(
+            reinterpret_cast<T2 *>(sv->data), N, tg, D);
+    }
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
 }
@@ -497,6 +565,7 @@ int sm_count_cached() {
 }
 
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g) {
+    if (oz_eligible(sv, g)) return launch_gate_oz(sv, g);
     if (sparse_preferred(sv, g)) return launch_gate_sparse(sv, g);
     if (tcc_eligible(sv, g)) return launch_gate_tcc(sv, g);
     if (tc_eligible(sv, g)) return launch_gate_tc(sv, g);

@@ -64,10 +64,9 @@ struct C64 {
     __device__ static void zero(Acc &a) { a = make_float2(0.f, 0.f); }
     __device__ static void merge(Acc &a, const Acc &b) { a.x += b.x; a.y += b.y; }
     template <int G>
-    __device__ static void apply(Acc (&y)[G], uint32_t kind, const Val *vp, const X *xs, int gs) {
+    __device__ static void apply(Acc (&y)[G], uint32_t kind, const Val u, const X *xs, int gs) {
         switch (kind) {
             case E_GEN: {
-                const float2 u = __ldg(vp);
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     const X x = xs[g * gs];
@@ -79,7 +78,7 @@ struct C64 {
                 break;
             }
             case E_RE: {
-                const float a = __ldg(&vp->x);
+                const float a = u.x;
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     const X x = xs[g * gs];
@@ -89,7 +88,7 @@ struct C64 {
                 break;
             }
             case E_IM: {
-                const float b = __ldg(&vp->y);
+                const float b = u.y;
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     const X x = xs[g * gs];
@@ -139,17 +138,16 @@ struct C128 {
         add(a.ih, a.il, b.ih, b.il);
     }
     template <int G>
-    __device__ static void apply(Acc (&y)[G], uint32_t kind, const Val *vp, const X *xs, int gs) {
+    __device__ static void apply(Acc (&y)[G], uint32_t kind, const Val u, const X *xs, int gs) {
         switch (kind) {
             case E_GEN: {
-                const float4 u = __ldg(vp);
                 const df::CF uc = {u.x, u.y, u.z, u.w};
 #pragma unroll
                 for (int g = 0; g < G; g++) df::cmac(y[g], uc, xs[g * gs]);
                 break;
             }
             case E_RE: {
-                const float2 a = __ldg(reinterpret_cast<const float2 *>(vp));
+                const float2 a = make_float2(u.x, u.y);
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     const X x = xs[g * gs];
@@ -159,7 +157,7 @@ struct C128 {
                 break;
             }
             case E_IM: {
-                const float2 b = __ldg(reinterpret_cast<const float2 *>(vp) + 1);
+                const float2 b = make_float2(u.z, u.w);
 #pragma unroll
                 for (int g = 0; g < G; g++) {
                     const X x = xs[g * gs];
@@ -193,12 +191,14 @@ struct C128 {
 // slices x 2^k members = 4096 amplitudes for every k): its 12 cube bits are
 // the 5 + log2 G lowest non-target positions and the k targets.  Each thread
 // moves 16 amplitudes per iteration; each entry of a row is decoded once and
-// applied to the G slices a lane owns.  For G <= 2 a row's entries alternate
-// between two accumulator sets (two independent dependency chains).
+// applied to the G slices a lane owns.  For G < 4 a row's entries alternate
+// between 4 / G accumulator sets, so every thread keeps four independent
+// dependency chains; an entry's code and value are loaded together, ahead of
+// the kind test that consumes them.
 template <int K> struct SpShape {
     static constexpr int D = 1 << K, G = 1 << (7 - K), E = 4096, PER = E / kSpThreads;
     static constexpr int RPW = D / kSpWarps;  // rows per warp
-    static constexpr int NCH = G <= 2 ? 2 : 1;
+    static constexpr int NCH = G >= 4 ? 1 : 4 / G;  // independent chains per row
 };
 
 template <class A, int K>
@@ -273,20 +273,29 @@ k_sparse(typename A::Amp *__restrict__ sv, uint64_t nsuper, const __grid_constan
                 for (int g = 0; g < G; g++) A::zero(acc[h][g]);
             const uint32_t e0 = __ldg(row_ptr + r), e1 = __ldg(row_ptr + r + 1);
             uint32_t e = e0;
-            if constexpr (NCH == 2) {
-                for (; e + 1 < e1; e += 2) {
-                    const uint32_t c0 = __ldg(code + e), c1 = __ldg(code + e + 1);
-                    A::template apply<G>(acc[0], c0 >> 8, val + e, Xs + (c0 & 0xFFu) * kSP + lane, GS);
-                    A::template apply<G>(acc[1], c1 >> 8, val + e + 1, Xs + (c1 & 0xFFu) * kSP + lane, GS);
+            if constexpr (NCH > 1) {
+                for (; e + NCH <= e1; e += NCH) {
+                    uint32_t c[NCH];
+                    typename A::Val u[NCH];
+#pragma unroll
+                    for (int h = 0; h < NCH; h++) {
+                        c[h] = __ldg(code + e + h);
+                        u[h] = __ldg(val + e + h);
+                    }
+#pragma unroll
+                    for (int h = 0; h < NCH; h++)
+                        A::template apply<G>(acc[h], c[h] >> 8, u[h], Xs + (c[h] & 0xFFu) * kSP + lane, GS);
                 }
             }
             for (; e < e1; e++) {
                 const uint32_t c = __ldg(code + e);
-                A::template apply<G>(acc[0], c >> 8, val + e, Xs + (c & 0xFFu) * kSP + lane, GS);
+                const typename A::Val u = __ldg(val + e);
+                A::template apply<G>(acc[0], c >> 8, u, Xs + (c & 0xFFu) * kSP + lane, GS);
             }
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                if constexpr (NCH == 2) A::merge(acc[0][g], acc[1][g]);
+#pragma unroll
+                for (int h = 1; h < NCH; h++) A::merge(acc[0][g], acc[h][g]);
                 y[i][g] = acc[0][g];
             }
         }
@@ -433,13 +442,17 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g) {
     const int64_t ops = opcount(g.m.data(), g.k, 0.0);
     if (sv->dt == CAST_C128) {
         if (f64_mode() != CAST_F64_EMULATED) return false;
-        // k = 6, 7 have no double-float dense kernel; below, the dense one wins when most entries are full
-        return g.k >= 6 || 4 * ops <= 3 * dense_opcount(g.k);
+        // measured at 30 qubits: the list kernel beats the unrolled double-float
+        // one for every k = 4 gate and for k = 3, 5 gates up to 3/4 of the
+        // dense operation count; k = 6, 7 have no other double-float kernel
+        return g.k == 4 || g.k >= 6 || 4 * ops <= 3 * dense_opcount(g.k);
     }
-    // complex64: FP32 work at HBM speed up to ~48 operations per amplitude
-    // (a pass of 2^30 amplitudes takes 2.6 ms; the FP32 pipe does ~34 T FMA/s)
-    if (g.k >= 5 && (ops >> g.k) <= 48) return true;
-    return !tensor_mode_tf32x3() && g.k >= 6;
+    // complex64: unitary gates of k >= 4 run on the tensor cores at about one
+    // memory pass (measured faster than the list at every density); other
+    // dense-class gates (non-unitary, or with the tensor cores off) on the
+    // CUDA cores, where the list kernel wins from k = 5 on and for sparse k = 4
+    if (tensor_mode_tf32x3() && g.unitary && g.k >= 4) return false;
+    return g.k >= 5 || (g.k == 4 && (ops >> g.k) <= 24);
 }
 
 cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g) {

@@ -470,6 +470,7 @@ cast_status take_device_error() {
     int v = 0;
     CAST_CUDA(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)));
     if (tcc_error_flag_take()) v = 1;
+    if (oz_error_flag_take()) v = 1;
     if (v) {
         const int zero = 0;
         CAST_CUDA(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));

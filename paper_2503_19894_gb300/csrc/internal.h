@@ -183,6 +183,12 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g);
 int64_t dense_opcount(int k);
 
+// Tensor-core complex128 path for dense k = 3..5 (apply_oz.cu): exact
+// products of 7-bit digits.
+bool oz_eligible(const cast_sv *sv, const PreparedGate &g);
+cast_status launch_gate_oz(cast_sv *sv, const PreparedGate &g);
+int oz_error_flag_take();
+
 // Double-float path for complex128 gates (apply_df.cu).
 bool df_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_df(cast_sv *sv, const PreparedGate &g);
