@@ -270,7 +270,12 @@ def secondary_dtype(n, layers, max_k, dtype, steps=1, warmup=1, native_f64=False
     torch.cuda.synchronize()
     prof = capi.cast_profile_end()
     ms = e0.elapsed_time(e1) / steps
-    arith = "double-float on FP32" if (S == 16 and capi.cast_get_f64_mode() == 0) else "native"
+    if S == 16 and capi.cast_get_f64_mode() == capi.CAST_F64_EMULATED:
+        arith = "double-float on FP32"
+        if capi.cast_get_c128_tensor_mode() == capi.CAST_C128_TC_OZAKI:
+            arith += "; dense k = 4, 5 as bf16 digit products on the tensor cores"
+    else:
+        arith = "native"
     sv.close()
     capi.cast_plan_destroy(pq)
     capi.cast_plan_destroy(pr)
@@ -548,6 +553,24 @@ def vqa_bench():
                              "grad_max_abs_4_params_each": g_err},
             "ms": {"batched_energy": round(t_e * 1e3, 2), "batched_grad": round(t_g * 1e3, 2),
                    "plain_energy_loop": round(t_p * 1e3, 1)}}
+    # the same 256 instances through the general batched executor (any
+    # circuit shape; the tile executor above is specialised to this ansatz)
+    for dt in ("c64", "c128"):
+        gb = capi.Batch([(n, gates, 2 * n * 10, W.tfim_hamiltonian(n, 0.5)) for n, gates, _ in batch],
+                        dtype=dt, with_grad=True)
+        t_e = _time(lambda: gb.energy(theta), 2)
+        t_g = _time(lambda: gb.grad(theta), 2)
+        energies = gb.energy(theta)
+        gb.close()
+        e_err = 0.0
+        for i in check:
+            n, gates, p = batch[i]
+            e_err = max(e_err, abs(energies[i] - oracle.energy(n, gates, p, W.tfim_hamiltonian(n, 0.5))))
+        out[f"batched_generic_{dt}"] = {
+            "instances": len(ns), "energies_per_s": round(len(ns) / t_e, 1), "grads_per_s": round(len(ns) / t_g, 1),
+            "grad_over_forward": round(t_g / t_e, 2), "gate_steps": int(max(len(g) for _, g, _ in batch)),
+            "oracle_check": {"instances": [int(ns[i]) for i in check], "energy_max_abs": e_err},
+            "ms": {"energy": round(t_e * 1e3, 1), "grad": round(t_g * 1e3, 1)}}
     n12, l12 = 12, 20
     g12, np12 = W.hea_ansatz(n12, l12)
     th12 = W.uniform_params(np12, -math.pi, math.pi, 44)

@@ -120,17 +120,16 @@ cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 
 /* complex128 dense gates on the tensor cores (process-wide setting):
- *   CAST_C128_TC_OFF (default): double-float arithmetic on the FP32 pipe;
- *   CAST_C128_TC_OZAKI: dense gates of k = 3..5 on states of n >= k + 7
+ *   CAST_C128_TC_OFF: double-float arithmetic on the FP32 pipe;
+ *   CAST_C128_TC_OZAKI (default): dense gates of k = 4, 5 on states of n >= k + 7
  *     qubits (in CAST_F64_EMULATED mode) as exact products of 7-bit digits
  *     on tcgen05 (kind::f16, bf16 operands, fp32 accumulation that never
  *     rounds for the three leading digit sums): each slice row and each row
  *     of the gate's real form is scaled by a power of two and cut to 49
- *     fractional bits, the digit-pair products with i + j <= 6 are
- *     accumulated by weight, and the result is assembled with integer
- *     operations; error ~2^-45 of the slice's largest amplitude.  Gates with
- *     at most a quarter of the dense operation count stay on the sparse
- *     kernel.  The paper has no tensor-core path; this is the complex128
+ *     fractional bits (rounded), the digit-pair products with i + j <= 6
+ *     are accumulated by weight, and the result is assembled with integer
+ *     operations; error ~2^-46 of the slice's largest amplitude.  Gates with
+ *     at most 60% of the dense operation count stay on the sparse kernel.  The paper has no tensor-core path; this is the complex128
  *     form of Eq. 3's matvec on GB300's tensor cores.
  * CAST_ERR_ARG for an unknown mode. */
 #define CAST_C128_TC_OFF 0
@@ -469,6 +468,43 @@ cast_status cast_hea_grad(cast_hea *b, const double *params, double zz, double h
 cast_status cast_hea_info(const cast_hea *b, int *n_params, int *n_passes_per_layer_max);
 
 cast_status cast_hea_destroy(cast_hea *b);
+
+/* ------------------------------------------------------------------------
+ * Batched variational circuits of any shape
+ * ---------------------------------------------------------------------- */
+
+/* A batch of circuit instances that need not share a shape: instance i has
+ * its own qubit count (1..30), gate list (1- and 2-qubit gates of any kind;
+ * RX, RY, RZ may carry a parameter: exp(-i theta P / 2)) and Pauli sum, and
+ * reads its parameters from the batch's parameter array starting at
+ * param_offsets[i] (NULL: instances' parameters stored one after the other;
+ * offsets may overlap to share parameters).  All states live in one arena,
+ * each starting at |0...0>.  Gate step s applies the s-th gate of every
+ * instance that has one in a single launch; rotation matrices are formed on
+ * the device from the parameters at every call, so the launch sequence is
+ * captured once into a CUDA graph and replayed for each parameter set.  The
+ * hardware-efficient ansatz has the faster tile executor (cast_hea_*); this is
+ * the general form.  Gradients use the adjoint method (two state vectors per
+ * instance, with_grad).  complex64 in FP32; complex128 in double-float
+ * arithmetic; energies and gradients accumulate in FP64.  The circuits and
+ * Pauli sums are copied; nothing the caller passed is kept. */
+typedef struct cast_batch cast_batch;
+
+cast_status cast_batch_create(int n_instances, const cast_circuit *circuits, const int32_t *param_offsets,
+                              const cast_pauli_sum *hamiltonians, cast_dtype dt, int with_grad,
+                              void *cuda_stream, cast_batch **out);
+
+/* energies[i] = <psi_i|H_i|psi_i> for the given parameters.  Waits. */
+cast_status cast_batch_energy(cast_batch *b, const double *params, double *energies);
+
+/* Energies plus dE_i/dparams (summed over the instances that read a
+ * parameter), by the adjoint method.  CAST_ERR_ARG without with_grad.  Waits. */
+cast_status cast_batch_grad(cast_batch *b, const double *params, double *energies, double *grads);
+
+/* Parameter array length and number of gate steps (the longest gate list). */
+cast_status cast_batch_info(const cast_batch *b, int *n_params, int *n_steps);
+
+cast_status cast_batch_destroy(cast_batch *b);
 
 /* Thread-local description of the last failure on this host thread. */
 const char *cast_last_error(void);

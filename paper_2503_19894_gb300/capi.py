@@ -76,7 +76,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_hea_create", "cast_hea_energy", "cast_hea_grad", "cast_hea_info", "cast_hea_destroy",
            "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table",
            "cast_debug_inject_timeout", "cast_measure_tensor_peak", "cast_set_sparse_mode",
-           "cast_get_sparse_mode", "cast_set_c128_tensor_mode", "cast_get_c128_tensor_mode")
+           "cast_get_sparse_mode", "cast_set_c128_tensor_mode", "cast_get_c128_tensor_mode",
+           "cast_batch_create", "cast_batch_energy", "cast_batch_grad", "cast_batch_info", "cast_batch_destroy")
 
 _lib = None
 
@@ -138,6 +139,11 @@ def load(build_if_missing=True):
         "cast_get_sparse_mode": (I, []),
         "cast_set_c128_tensor_mode": (I, [I]),
         "cast_get_c128_tensor_mode": (I, []),
+        "cast_batch_create": (I, [I, P, P, P, I, I, P, PP]),
+        "cast_batch_energy": (I, [P, P, P]),
+        "cast_batch_grad": (I, [P, P, P, P]),
+        "cast_batch_info": (I, [P, P, P]),
+        "cast_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -538,3 +544,49 @@ def cast_last_error():
 
 def cast_version():
     return load().cast_version().decode()
+
+
+# ------------------------------------------- batched circuits of any shape
+
+class Batch:
+    """A cast_batch: instances = [(n_qubits, gates, n_params, terms)], each
+    instance's parameters one after the other in the parameter array (or at
+    param_offsets)."""
+
+    def __init__(self, instances, dtype="c64", with_grad=False, param_offsets=None, stream=0):
+        self._circs = [_Circuit(n, gates, npar) for n, gates, npar, _ in instances]
+        self._hams = [_Pauli(terms) for _, _, _, terms in instances]
+        circ_arr = (cast_circuit * len(instances))(*[c.c for c in self._circs])
+        ham_arr = (cast_pauli_sum * len(instances))(*[h.s for h in self._hams])
+        offs = None
+        if param_offsets is not None:
+            self._offs = np.ascontiguousarray(param_offsets, dtype=np.int32)
+            offs = ctypes.c_void_p(self._offs.ctypes.data)
+        h = ctypes.c_void_p()
+        _check(load().cast_batch_create(len(instances), ctypes.byref(circ_arr), offs, ctypes.byref(ham_arr),
+                                        _dt(dtype), int(bool(with_grad)), ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.handle = h.value
+        self.n_instances = len(instances)
+        npar, nsteps = ctypes.c_int(), ctypes.c_int()
+        _check(load().cast_batch_info(ctypes.c_void_p(self.handle), ctypes.byref(npar), ctypes.byref(nsteps)))
+        self.n_params, self.n_steps = npar.value, nsteps.value
+
+    def energy(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        e = np.zeros(self.n_instances)
+        _check(load().cast_batch_energy(ctypes.c_void_p(self.handle), ctypes.c_void_p(p.ctypes.data if p.size else None),
+                                        ctypes.c_void_p(e.ctypes.data)))
+        return e
+
+    def grad(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        e = np.zeros(self.n_instances)
+        g = np.zeros(max(1, self.n_params))
+        _check(load().cast_batch_grad(ctypes.c_void_p(self.handle), ctypes.c_void_p(p.ctypes.data if p.size else None),
+                                      ctypes.c_void_p(e.ctypes.data), ctypes.c_void_p(g.ctypes.data)))
+        return e, g[:self.n_params]
+
+    def close(self):
+        if self.handle:
+            _check(load().cast_batch_destroy(ctypes.c_void_p(self.handle)))
+            self.handle = None

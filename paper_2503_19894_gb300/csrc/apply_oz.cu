@@ -1,4 +1,4 @@
-// Dense complex128 gates (k = 3, 4, 5) on the tcgen05 tensor cores with an
+// Dense complex128 gates (k = 4, 5) on the tcgen05 tensor cores with an
 // Ozaki-style split into exactly multiplied integer digits (Ozaki, Ogita and
 // Oishi 2012; Ootomo, Ozaki and Yokota 2024 for the GPU form).
 //
@@ -8,50 +8,55 @@
 // (2x2 blocks [[a, -b], [b, a]] for u = a + ib), as in the complex64 kernel.
 //
 // Splitting.  Each slice row r of X gets an exponent E_r with every |x| <
-// 2^E_r; x / 2^E_r is cut to 49 fractional bits (truncation error below
-// 2^(E_r - 49)) and written as seven 7-bit digits, x = 2^E_r sum_i a_i
-// 2^(-7(i+1)), a_i in [-127, 127] (all digits carry the sign of x).  Each
+// 2^E_r; x / 2^E_r is rounded to 49 fractional bits (error at most
+// 2^(E_r - 50), unbiased) and written as seven 7-bit digits, x = 2^E_r
+// sum_i a_i 2^(-7(i+1)), a_i in [-127, 127] (all digits carry the sign of x).  Each
 // output row n of W is split the same way with its own exponent E_n into
 // digits w_j.  Digits are stored pre-scaled, a_i 2^(-7i) and w_j 2^(-7j),
 // which bf16 represents exactly (7 significant bits times a power of two).
 //
-// Products.  For every pair (i, j) with i + j <= 6 one tcgen05.mma per
+// Products.  For every pair (i, j) with i + j <= 7 one tcgen05.mma per
 // K-step (kind::f16, bf16 operands, fp32 accumulation; A = digit i of X from
 // tensor memory, B = digit j of W from shared memory) adds a_i w_j 2^(-7(i+j))
-// into accumulator min(i + j, 4).  Accumulators d = 0..3 only ever hold
-// integers times 2^(-7d) of magnitude below (d + 1) * 2D * 127^2 <= 4.13e6 <
-// 2^22 (in units of 2^(-7d)), so they are exact in fp32 whatever the order
-// of the additions or the rounding of the tensor cores; accumulator 4 gathers
-// the products of weight 2^-28 and below, where the fp32 accumulation
-// (measured: it truncates, so its errors add up over the MMAs) costs about
-// 2^-43 of the output.  Dropping the pairs with i + j > 6 costs about 2^-49.
-// (A design that let d = 3 share the inexact accumulator measured 3.5e-12
-// relative error: 2^-21-weighted sums truncated over ~90 MMAs.)
+// into accumulator min(i + j, 5).  Accumulators d = 0..4 only ever hold
+// integers times 2^(-7d) of magnitude below (d + 1) * 2D * 127^2 <= 5.2e6 <
+// 2^24 (in units of 2^(-7d)), so they are exact in fp32 whatever the order
+// of the additions or the rounding of the tensor cores; accumulator 5 gathers
+// the products of weight 2^-35 and below, where the fp32 accumulation
+// (it truncates, so its errors add up over the MMAs) costs about 2^-50 of
+// the output.  The dropped pairs (i + j >= 8) are all of the sign of their
+// product (every digit carries the sign of its value), so they shrink the
+// outputs by ~2^-53; with i + j <= 6 only, that bias was 2^-46 and the norm
+// of a state fell by 6.5e-12 over 200 gates.  Measured: a design that let
+// weights 2^-21 and below share one inexact accumulator was 3.5e-12 off, one
+// that let 2^-28 and below share it 1.8e-13 off (relative to the slice's
+// scale), against 1.5e-13 for a 2^-28 common integer scale alone: both limits
+// are gone here.
 //
-// Epilogue.  y = 2^(E_r + E_n - 14) (acc0 + ... + acc4): acc_d 2^(7d) for
+// Epilogue.  y = 2^(E_r + E_n - 14) (acc0 + ... + acc5): acc_d 2^(7d) for
 // d <= 3 are converted to integers exactly (fp32 magic-number rounding of an
-// exact integer below 2^22), acc4 * 2^28 is rounded to an integer, the five are
-// summed in 64-bit integer arithmetic at the common scale 2^-28 and the
-// result is written as an FP64 with integer operations (leading-zero count,
-// shift, exponent), so no FP64 instruction runs on the device.  The result is
-// within ~2^-43 of the row's scale 2^(E_r + E_n) (about 1e-13 of the largest
-// amplitude of a slice).
+// exact integer below 2^22), acc4 * 2^28 (an exact integer below 2^24) and
+// acc5 * 2^36 are converted with rounding, the six are summed in 64-bit
+// integer arithmetic at the common scale 2^-36 and the result is written as
+// an FP64 with integer operations (leading-zero count, shift, exponent), so no
+// FP64 instruction runs on the device.
 //
 // Tensor memory holds the seven digits of A (D columns each, two bf16 per
-// column) and five accumulators; for k = 4, 5 the outputs are produced in two
+// column) and six accumulators; for k = 4, 5 the outputs are produced in two
 // halves of D columns (MMAs of half the N, then that half's epilogue) so that
-// five accumulators fit beside the digits.
+// six accumulators fit beside the digits.
 //
-// Data path: 128 threads (4 warps), thread = slice row = TMEM lane.  A tile's
-// 128 slice rows are loaded with 16-byte loads into shared memory
-// ([member][thread]), the exponents and digits are formed from there and
-// stored to tensor memory with tcgen05.st; one thread issues the MMAs and
+// Data path: 256 threads (8 warps), two per slice row (TMEM lane), each with
+// half of the row's members.  A tile's 128 slice rows are loaded with 16-byte
+// loads into shared memory ([member][row]); the two halves' exponents meet in
+// shared memory; each thread forms the digits of its members once per real
+// and stores them to tensor memory with tcgen05.st; one thread issues the MMAs and
 // commits them to an mbarrier; while they run, every thread loads the next
 // tile into shared memory; the epilogue reads the four accumulators with
 // tcgen05.ld and stores the outputs.  W's digits (host-built, already in the
 // 128-byte-swizzled K-major shared-memory image) are copied in once per CTA.
-// TMEM per CTA: 7 x D digit columns + 5 x 2D / NH accumulator columns (NH
-// output halves): 136 / 192 / 384 for k = 3 / 4 / 5, so 2 / 2 / 1 CTAs per SM.
+// TMEM per CTA: 7 x D digit columns + 6 x 2D / NH accumulator columns (NH
+// output halves): 152 / 208 / 416 for k = 3 / 4 / 5, so 2 / 2 / 1 CTAs per SM.
 // Waits on the mbarrier are bounded (error flag, no trap).
 #include <cuda_runtime.h>
 
@@ -72,7 +77,7 @@ int oz_error_flag_take();
 namespace {
 
 __device__ int g_oz_error;
-std::atomic<int> g_c128_tc{CAST_C128_TC_OFF};
+std::atomic<int> g_c128_tc{CAST_C128_TC_OZAKI};
 constexpr uint32_t kOzWait = 1u << 26;
 constexpr int kDigits = 7;
 
@@ -84,12 +89,12 @@ struct OzShape {
     static constexpr int DCOL = NR / 2;      // TMEM columns of one digit (two bf16 per column)
     static constexpr int NH = K >= 4 ? 2 : 1;  // output halves (MMA N >= 16)
     static constexpr int NHW = NR / NH;        // outputs per half = MMA N
-    static constexpr int NACC = 5;
+    static constexpr int NACC = 6;
     static constexpr int ACOL0 = kDigits * DCOL;  // first accumulator column
     static constexpr int NCOL_USED = ACOL0 + NACC * NHW;
     static constexpr int NCOL = NCOL_USED <= 128 ? 128 : (NCOL_USED <= 256 ? 256 : 512);
     static constexpr int WBYTES = kDigits * NR * 128;  // W digits: N rows of 128 bytes per digit
-    static constexpr int SBYTES = 128 * D * 16;        // staged tile: [member][thread] double2
+    static constexpr int SBYTES = 128 * D * 16;        // staged tile: [member][row] double2
 };
 
 struct OzParams {
@@ -120,20 +125,24 @@ __device__ __forceinline__ double i64_to_double(int64_t Y, int e) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
            const uint8_t *__restrict__ wimg, const __grid_constant__ OzParams P, uint32_t wait_limit) {
     using S = OzShape<K>;
-    constexpr int D = S::D, NR = S::NR;
+    constexpr int D = S::D, NR = S::NR, NHW = S::NHW, NACC = S::NACC;
+    constexpr int DH = D / 2;     // members of a row this thread handles
+    constexpr int OH = NHW / 2;   // outputs of an output half this thread finishes
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sW = base;                                              // W digits (1024-aligned)
-    double2 *stg = reinterpret_cast<double2 *>(sW + S::WBYTES);      // [member][thread]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(stg + 128 * D);
+    double2 *stg = reinterpret_cast<double2 *>(sW + S::WBYTES);      // [member][row]
+    int *sE = reinterpret_cast<int *>(stg + 128 * D);                // [half][row] partial exponents
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sE + 256);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, half = tid >> 7;  // slice row = TMEM lane; members [half * DH, half * DH + DH)
 
-    for (int i = tid; i < S::WBYTES / 16; i += 128)
+    for (int i = tid; i < S::WBYTES / 16; i += 256)
         reinterpret_cast<uint4 *>(sW)[i] = __ldg(reinterpret_cast<const uint4 *>(wimg) + i);
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
@@ -142,24 +151,27 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
-    const uint32_t lane_addr = taddr + (uint32_t(32 * warp) << 16);
+    const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
 
     uint64_t p[K];
 #pragma unroll
     for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
+    auto member_off = [&](int j) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if ((j >> i) & 1) off += p[i];
+        return off;
+    };
     auto load_tile = [&](uint64_t t) {
-        const uint64_t b = slice_base<K>(t * 128 + tid, tg);
+        const uint64_t b = slice_base<K>(t * 128 + row, tg);
 #pragma unroll
-        for (int j = 0; j < D; j++) {
-            uint64_t off = 0;
-#pragma unroll
-            for (int i = 0; i < K; i++)
-                if ((j >> i) & 1) off += p[i];
-            stg[j * 128 + tid] = __ldcs(sv + b + off);
+        for (int jj = 0; jj < DH; jj++) {
+            const int j = half * DH + jj;
+            stg[j * 128 + row] = __ldcs(sv + b + member_off(j));
         }
     };
 
-    constexpr int NHW = S::NHW;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NHW >> 3) << 17) | (uint32_t(128 >> 4) << 24);
     const uint32_t wbase = tc::smem_u32(sW);
     uint32_t phase = 0;
@@ -167,40 +179,50 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
     uint64_t tile = blockIdx.x;
     if (tile < ntiles) load_tile(tile);
     while (tile < ntiles) {
-        // ---- row exponent and digits of this thread's slice row
-        int er = -1022;
+        // ---- row exponent: both halves' maxima
+        int eh = -1022;
 #pragma unroll
-        for (int j = 0; j < D; j++) {
-            const double2 v = stg[j * 128 + tid];
+        for (int jj = 0; jj < DH; jj++) {
+            const double2 v = stg[(half * DH + jj) * 128 + row];
             const int e0 = int((__double_as_longlong(v.x) >> 52) & 0x7FF), e1 = int((__double_as_longlong(v.y) >> 52) & 0x7FF);
-            er = max(er, max(e0, e1) - 1022);
+            eh = max(eh, max(e0, e1) - 1022);
         }
-        // fixed-point magnitude with 49 fractional bits below 2^er, and sign
-        auto fixed = [&](double x, uint32_t &sign) -> uint64_t {
-            const uint64_t b = uint64_t(__double_as_longlong(x));
-            sign = uint32_t(b >> 32) & 0x80000000u;
-            const int e = int((b >> 52) & 0x7FF);
-            if (e == 0) return 0;  // zero or subnormal (< 2^-1022)
-            const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
-            const int sh = 4 + (er - (e - 1022));  // m * 2^(e - 1075 - er + 49)
-            return sh >= 53 ? 0 : (m >> sh);
-        };
+        sE[half * 128 + row] = eh;
+        __syncthreads();
+        const int er = max(sE[row], sE[128 + row]);
+        // ---- digits of this thread's members, in chunks of (up to) 8 members
+        constexpr int CH = DH < 8 ? DH : 8;
 #pragma unroll
-        for (int i = 0; i < kDigits; i++) {
-            // digit i of the 2D reals: 2D bf16 = D columns, in chunks of 8 columns
+        for (int c0 = 0; c0 < DH; c0 += CH) {
+            uint64_t F[2 * CH];  // fixed-point magnitudes, 49 fractional bits below 2^er
+            uint32_t sg[2 * CH];
 #pragma unroll
-            for (int c0 = 0; c0 < D; c0 += 8) {
-                float v8[8];
+            for (int c = 0; c < CH; c++) {
+                const double2 x = stg[(half * DH + c0 + c) * 128 + row];
 #pragma unroll
-                for (int c = 0; c < 8; c++) {
-                    const double2 x = stg[(c0 + c) * 128 + tid];  // reals 2(c0+c), 2(c0+c)+1
-                    uint32_t s0, s1;
-                    const uint64_t f0 = fixed(x.x, s0), f1 = fixed(x.y, s1);
-                    const int sh = 7 * (kDigits - 1 - i);
-                    const uint32_t a0 = uint32_t(f0 >> sh) & 127u, a1 = uint32_t(f1 >> sh) & 127u;
-                    v8[c] = __uint_as_float(digit_bf16(a0, i, s0) | (digit_bf16(a1, i, s1) << 16));
+                for (int part = 0; part < 2; part++) {
+                    const uint64_t bits = uint64_t(__double_as_longlong(part ? x.y : x.x));
+                    const int e = int((bits >> 52) & 0x7FF);
+                    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
+                    const int sh = 4 + (er - (e - 1022));
+                    // nearest 49-bit fraction (unbiased: truncation would shrink every
+                    // product and the error would build up over a circuit); a value
+                    // that rounds up to 2^er keeps the largest fraction below it
+                    const uint64_t f = (e == 0 || sh >= 54) ? 0 : ((m >> (sh - 1)) + 1) >> 1;
+                    F[2 * c + part] = f < (uint64_t(1) << 49) ? f : (uint64_t(1) << 49) - 1;
+                    sg[2 * c + part] = uint32_t(bits >> 32) & 0x80000000u;
                 }
-                tc::tmem_st<8>(lane_addr + uint32_t(i * S::DCOL + c0), v8);
+            }
+#pragma unroll
+            for (int i = 0; i < kDigits; i++) {
+                float v[CH];
+                const int sh = 7 * (kDigits - 1 - i);
+#pragma unroll
+                for (int c = 0; c < CH; c++) {
+                    const uint32_t a0 = uint32_t(F[2 * c] >> sh) & 127u, a1 = uint32_t(F[2 * c + 1] >> sh) & 127u;
+                    v[c] = __uint_as_float(digit_bf16(a0, i, sg[2 * c]) | (digit_bf16(a1, i, sg[2 * c + 1]) << 16));
+                }
+                tc::tmem_st<CH>(lane_addr + uint32_t(i * S::DCOL + half * DH + c0), v);
             }
         }
         tc::tmem_wait_st();
@@ -209,18 +231,20 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         tc::fence_after_sync();
         const uint64_t next = tile + gridDim.x;
         const int er_cur = er;
-        const uint64_t ob = slice_base<K>(tile * 128 + tid, tg);
+        const uint64_t ob = slice_base<K>(tile * 128 + row, tg);
 #pragma unroll
         for (int h = 0; h < S::NH; h++) {
             if (tid == 0) {
-                bool first[S::NACC] = {true, true, true, true, true};
+                bool first[NACC];
 #pragma unroll
-                for (int d = 0; d < S::NACC; d++) {
+                for (int d = 0; d < NACC; d++) first[d] = true;
+#pragma unroll
+                for (int d = 0; d < NACC; d++) {
 #pragma unroll
                     for (int i = 0; i < kDigits; i++) {
 #pragma unroll
-                        for (int j = 0; j < kDigits - i; j++) {
-                            if ((i + j < S::NACC - 1 ? i + j : S::NACC - 1) != d) continue;
+                        for (int j = 0; j < kDigits && i + j <= kDigits; j++) {
+                            if ((i + j < NACC - 1 ? i + j : NACC - 1) != d) continue;
 #pragma unroll
                             for (int ks = 0; ks < S::KS; ks++) {
                                 const uint64_t bdesc =
@@ -242,38 +266,38 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
             __syncwarp();
             if (h == 0) {
                 // ---- the next tile's loads run while the MMAs execute
-                __syncthreads();  // every thread has read the staged tile
+                __syncthreads();  // every thread has read the staged tile and the exponents
                 if (next < ntiles) load_tile(next);
             }
             failed = __syncthreads_or(!tc::mbar_wait(mbar, phase, wait_limit));  // agreed by all threads
             if (failed) break;
             phase ^= 1u;
             tc::fence_after_sync();
-            // ---- epilogue of this half: y = 2^(E_r + E_n - 14) (acc0 + ... + acc4)
+            // ---- epilogue of outputs [h NHW + half OH, + OH): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
+            constexpr int EC = OH < 16 ? OH : 16;
 #pragma unroll
-            for (int n0 = 0; n0 < NHW; n0 += 16) {
-                float ac[S::NACC][16];
+            for (int n0 = 0; n0 < OH; n0 += EC) {
+                const int col = half * OH + n0;  // within this output half
+                float ac[NACC][EC];
 #pragma unroll
-                for (int d = 0; d < S::NACC; d++) tc::tmem_ld<16>(lane_addr + uint32_t(S::ACOL0 + d * NHW + n0), ac[d]);
+                for (int d = 0; d < NACC; d++) tc::tmem_ld<EC>(lane_addr + uint32_t(S::ACOL0 + d * NHW + col), ac[d]);
 #pragma unroll
-                for (int m = 0; m < 8; m++) {
+                for (int m = 0; m < EC / 2; m++) {
                     double out[2];
 #pragma unroll
                     for (int hh = 0; hh < 2; hh++) {
                         const int c = 2 * m + hh;
-                        const int64_t Y = (int64_t(exact_int(ac[0][c])) << 28) +
-                                          (int64_t(exact_int(ac[1][c] * 128.0f)) << 21) +
-                                          (int64_t(exact_int(ac[2][c] * 16384.0f)) << 14) +
-                                          (int64_t(exact_int(ac[3][c] * 2097152.0f)) << 7) +
-                                          int64_t(__float2int_rn(ac[4][c] * 268435456.0f));
-                        out[hh] = i64_to_double(Y, er_cur + int(P.wexp[h * NHW + n0 + c]) - 28);
+                        // common scale 2^-36 (in units of the weight-0 products)
+                        const int64_t Y = (int64_t(exact_int(ac[0][c])) << 36) +
+                                          (int64_t(exact_int(ac[1][c] * 128.0f)) << 29) +
+                                          (int64_t(exact_int(ac[2][c] * 16384.0f)) << 22) +
+                                          (int64_t(exact_int(ac[3][c] * 2097152.0f)) << 15) +
+                                          (int64_t(__float2int_rn(ac[4][c] * 268435456.0f)) << 8) +
+                                          int64_t(__float2int_rn(ac[5][c] * 68719476736.0f));
+                        out[hh] = i64_to_double(Y, er_cur + int(P.wexp[h * NHW + col + c]) - 36);
                     }
-                    const int j = ((h * NHW + n0) >> 1) + m;
-                    uint64_t off = 0;
-#pragma unroll
-                    for (int i = 0; i < K; i++)
-                        if ((j >> i) & 1) off += p[i];
-                    __stcs(sv + ob + off, make_double2(out[0], out[1]));
+                    const int j = ((h * NHW + col) >> 1) + m;
+                    __stcs(sv + ob + member_off(j), make_double2(out[0], out[1]));
                 }
             }
             tc::fence_before_sync();
@@ -298,11 +322,12 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 }
 
 // ----------------------------------------------------------------- host side
-// Seven 7-bit digits of |w| / 2^E (49 fractional bits, truncated), E with
-// every |w| of the row below 2^E.
+// Seven 7-bit digits of |w| / 2^E (49 fractional bits, rounded to nearest,
+// at most 2^49 - 1), E with every |w| of the row below 2^E.
 void host_digits(double w, int E, int *dig) {
-    const double f = std::floor(std::ldexp(std::fabs(w), 49 - E));  // < 2^49, exact
+    const double f = std::nearbyint(std::ldexp(std::fabs(w), 49 - E));  // <= 2^49, exact
     uint64_t F = uint64_t(f);
+    if (F >= (uint64_t(1) << 49)) F = (uint64_t(1) << 49) - 1;
     for (int j = kDigits - 1; j >= 0; j--) {
         dig[j] = int(F & 127u);
         F >>= 7;
@@ -367,14 +392,14 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     Targets tg;
     for (int i = 0; i < CAST_MAX_K; i++) tg.q[i] = i < K ? g.q[i] : 0;
     const uint64_t ntiles = uint64_t(1) << (sv->n - K - 7);
-    const size_t smem = 1024 + S::WBYTES + S::SBYTES + 64;
+    const size_t smem = 1024 + S::WBYTES + S::SBYTES + 256 * 4 + 64;
     CAST_CUDA(cudaFuncSetAttribute(k_dense_oz<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int per_sm = 512 / S::NCOL;
     const uint64_t cap = uint64_t(sm_count_cached()) * per_sm;
     const uint64_t grid = ntiles < cap ? ntiles : cap;
     const double N = double(uint64_t(1) << sv->n);
     ProfScope ps(sv->stream, "ozdense_k" + std::to_string(K) + "_c128", 32.0 * N, 8.0 * N * double(D));
-    k_dense_oz<K><<<(unsigned)grid, 128, smem, sv->stream>>>(reinterpret_cast<double2 *>(sv->data), ntiles, tg,
+    k_dense_oz<K><<<(unsigned)grid, 256, smem, sv->stream>>>(reinterpret_cast<double2 *>(sv->data), ntiles, tg,
                                                              static_cast<const uint8_t *>(dev), P, kOzWait);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
@@ -384,19 +409,21 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
 
 bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
-        g.cls != CLS_DENSE || g.k < 3 || g.k > 5 || sv->n < g.k + 7)
+        g.cls != CLS_DENSE || g.k < 4 || g.k > 5 || sv->n < g.k + 7)
         return false;
-    // gates with at most a quarter of the dense operation count stay on the
-    // sparse kernel
-    return 4 * opcount(g.m.data(), g.k, 0.0) > dense_opcount(g.k);
+    // measured per 30-qubit gate: this kernel 22-23 ms (k = 4) and 32-38 ms
+    // (k = 5) whatever the matrix; the sparse kernel 10-12 / 11-20 ms at 10-30%
+    // density and 35 / 62-69 ms dense: the digit kernel takes the gates above
+    // 60% of the dense operation count (k = 3 gates stay on the CUDA cores,
+    // where the sparse and dense double-float kernels match it)
+    return 5 * opcount(g.m.data(), g.k, 0.0) > 3 * dense_opcount(g.k);
 }
 
 cast_status launch_gate_oz(cast_sv *sv, const PreparedGate &g) {
     switch (g.k) {
-        case 3: return run_oz<3>(sv, g);
         case 4: return run_oz<4>(sv, g);
         case 5: return run_oz<5>(sv, g);
-        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 3..5");
+        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 4, 5");
     }
 }
 

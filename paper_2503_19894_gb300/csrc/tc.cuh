@@ -156,6 +156,12 @@ __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float (&v)[16]
         : "memory");
 }
 template <>
+__device__ __forceinline__ void tmem_st<4>(uint32_t taddr, const float (&v)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
+template <>
 __device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const float (&v)[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "f"(v[0]),
                  "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
@@ -168,6 +174,16 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
 template <>
 __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
     tmem_ld32(taddr, v);
+}
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
