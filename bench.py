@@ -451,10 +451,12 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
     families = families or list(W.FAMILIES)
     out = {"n_qubits": n, "families": {}, "autotune_s": {}}
     tables = {}
+    out["cost_tables"] = {}
     for dt in dtypes:
         t0 = time.perf_counter()
         tables[dt] = capi.cast_autotune(dt, n)
         out["autotune_s"][dt] = round(time.perf_counter() - t0, 1)
+        out["cost_tables"][dt] = capi.cost_table_dict(tables[dt])
     for fam in families:
         gates = W.benchmark_family(fam, n)
         fam_out = {"class": W.FAMILIES[fam][1], "input_gates": len(gates)}
@@ -462,6 +464,7 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
             S = 8 if dt == "c64" else 16
             modes = (("none", capi.options("none", 5)), ("size_k5", capi.options("size", 5)),
                      ("adaptive_k5", capi.options("adaptive", 5)),
+                     ("adaptive_measured_k5", capi.options("adaptive", 5, cost=tables[dt])),
                      ("adaptive_measured_width_search", capi.options("adaptive", 0, cost=tables[dt])))
             sv = pkg.StateVector(n, dt, init_index=W.random_basis_index(n, 1))
             res = {}
@@ -478,10 +481,14 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1)
+                capi.cast_profile_begin()  # per kernel family, one more application
+                capi.cast_plan_apply(sv.handle, plan)
+                prof = capi.cast_profile_end()
                 capi.cast_plan_destroy(plan)
                 res[name] = {"fused_gates": count, "compression": round(len(gates) / max(1, count), 2),
                              "total_ops": ops, "host_fusion_ms": round(host_ms, 1), "device_ms": round(ms, 1),
-                             "gbs": round(count * 2.0 * (1 << n) * S / (ms / 1e3) / 1e9, 1)}
+                             "gbs": round(count * 2.0 * (1 << n) * S / (ms / 1e3) / 1e9, 1),
+                             "kernels": {p["name"]: [p["launches"], round(p["ms"], 2)] for p in prof}}
             none_ms = res["none"]["device_ms"]
             for r in res.values():
                 r["time_vs_none"] = round(r["device_ms"] / none_ms, 4)

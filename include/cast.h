@@ -145,10 +145,12 @@ int cast_get_c128_tensor_mode(void);
  * additions); entries within 1e-14 of +-1 or +-i count as exactly that value
  * (the paper's one tolerance).  Process-wide setting:
  *   CAST_SPARSE_AUTO (default): complex128 (double-float mode) gates of
- *     k = 4, 6, 7, and of k = 3, 5 with at most 3/4 of the dense operation
+ *     k = 4 (those the tensor-core digit kernel leaves), 6, 7, and of
+ *     k = 3, 5 with at most 3/4 of the dense operation
  *     count; complex64 dense-class gates that the tensor cores do not take
- *     (non-unitary, or tensor cores off) of k >= 5, and of k = 4 with at
- *     most 24 operations per amplitude;
+ *     (non-unitary, or tensor cores off) of k = 4 with at most 24
+ *     operations per amplitude, k = 5 with at most 80% and k = 6, 7 with at
+ *     most 40% of the dense operation count;
  *   CAST_SPARSE_OFF: never;  CAST_SPARSE_ALWAYS: every dense-class gate of
  *     k = 3..7 (complex128 only in double-float mode).
  * States need n >= 12.  CAST_ERR_ARG for an unknown mode. */

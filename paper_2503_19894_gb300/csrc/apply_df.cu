@@ -108,6 +108,47 @@ k_diag_df(double2 *__restrict__ sv, uint64_t N, Targets tg, const __grid_constan
     }
 }
 
+// Chunked form for states of at least 2^11 amplitudes (as k_diag_chunk in
+// apply.cu): a CTA iteration covers 256 x 8 consecutive amplitudes (thread t
+// takes t, t + 256, ...); the diagonal index is the OR of the chunk's part,
+// the thread's part and the round's part (rounds from the launch parameters).
+struct DfChunkBits {
+    int jr[8];
+};
+
+template <int K>
+__global__ void __launch_bounds__(256)
+k_diag_df_chunk(double2 *__restrict__ sv, uint64_t nchunks, const __grid_constant__ Targets tg,
+                const __grid_constant__ DfDiag<K> Dg, const __grid_constant__ DfChunkBits cb) {
+    constexpr int UNR = 8, CB = 11;
+    auto jbits = [&](uint64_t x) {
+        int j = 0;
+#pragma unroll
+        for (int b = 0; b < K; b++) j |= int((x >> tg.q[b]) & 1) << b;
+        return j;
+    };
+    const int jt = jbits(uint64_t(threadIdx.x));
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint64_t base = c << CB;
+        const int jh = jbits(base) | jt;
+        double2 *p = sv + base + threadIdx.x;
+        uint32_t act = 0;
+#pragma unroll
+        for (int u = 0; u < UNR; u++) act |= uint32_t(K > 5 || !((Dg.skip >> (jh | cb.jr[u])) & 1)) << u;
+        double2 v[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++)
+            if ((act >> u) & 1) v[u] = p[256 * u];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            if (!((act >> u) & 1)) continue;
+            CF acc = {0.f, 0.f, 0.f, 0.f};
+            cmac(acc, Dg.d[jh | cb.jr[u]], split_c(v[u]));
+            p[256 * u] = join_c(acc);
+        }
+    }
+}
+
 template <int K>
 struct DfMono {
     CF ph[1 << K];
@@ -168,8 +209,18 @@ cast_status run_k(cast_sv *sv, const PreparedGate &g) {
         const double frac = double(touched) / double(1 << K);
         ProfScope ps(sv->stream, "dfdiag_k" + std::to_string(K) + "_c128", 32.0 * double(N) * frac,
                      6.0 * double(N) * frac);
-        k_diag_df<K><<<(unsigned)grid_for(N / 4, tuned_blocks_per_sm(CAST_C128, K, CLS_DIAG, 8)), 256, 0,
-                       sv->stream>>>(data, N, tg, Dg);
+        if (sv->n >= 11) {
+            DfChunkBits cb{};
+            for (int u = 0; u < 8; u++)
+                for (int b = 0; b < K; b++) cb.jr[u] |= int(((uint64_t(u) << 8) >> g.q[b]) & 1) << b;
+            const uint64_t nchunks = N >> 11;
+            const uint64_t cap = uint64_t(sm_count_cached()) * tuned_blocks_per_sm(CAST_C128, K, CLS_DIAG, 8);
+            k_diag_df_chunk<K><<<(unsigned)(nchunks < cap ? nchunks : cap), 256, 0, sv->stream>>>(data, nchunks, tg,
+                                                                                                  Dg, cb);
+        } else {
+            k_diag_df<K><<<(unsigned)grid_for(N / 4, tuned_blocks_per_sm(CAST_C128, K, CLS_DIAG, 8)), 256, 0,
+                           sv->stream>>>(data, N, tg, Dg);
+        }
     } else {
         DfMono<K> M;
         for (int j = 0; j < (1 << K); j++) {

@@ -46,10 +46,10 @@
 // halves of D columns (MMAs of half the N, then that half's epilogue) so that
 // six accumulators fit beside the digits.
 //
-// Data path: 256 threads (8 warps), two per slice row (TMEM lane), each with
-// half of the row's members.  A tile's 128 slice rows are loaded with 16-byte
-// loads into shared memory ([member][row]); the two halves' exponents meet in
-// shared memory; each thread forms the digits of its members once per real
+// Data path: four threads per slice row (TMEM lane),
+// each with its share of the row's members.  A tile's 128 slice rows are
+// loaded with 16-byte loads into shared memory ([member][row]); the parts'
+// exponents meet in shared memory; each thread forms the digits of its members once per real
 // and stores them to tensor memory with tcgen05.st; one thread issues the MMAs and
 // commits them to an mbarrier; while they run, every thread loads the next
 // tile into shared memory; the epilogue reads the four accumulators with
@@ -95,6 +95,11 @@ struct OzShape {
     static constexpr int NCOL = NCOL_USED <= 128 ? 128 : (NCOL_USED <= 256 ? 256 : 512);
     static constexpr int WBYTES = kDigits * NR * 128;  // W digits: N rows of 128 bytes per digit
     static constexpr int SBYTES = 128 * D * 16;        // staged tile: [member][row] double2
+    // four threads per slice row: k = 4 two CTAs of 16 warps per SM (TMEM 2 x
+    // 256 columns, 64 registers), k = 5 one CTA of 16 warps (416 columns)
+    static constexpr int R = 4;
+    static constexpr int NT = 128 * R;
+    static constexpr int MIN_CTAS = K == 4 ? 2 : 1;
 };
 
 struct OzParams {
@@ -125,24 +130,26 @@ __device__ __forceinline__ double i64_to_double(int64_t Y, int e) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(OzShape<K>::NT, OzShape<K>::MIN_CTAS)
 k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
            const uint8_t *__restrict__ wimg, const __grid_constant__ OzParams P, uint32_t wait_limit) {
     using S = OzShape<K>;
     constexpr int D = S::D, NR = S::NR, NHW = S::NHW, NACC = S::NACC;
-    constexpr int DH = D / 2;     // members of a row this thread handles
-    constexpr int OH = NHW / 2;   // outputs of an output half this thread finishes
+    constexpr int R = S::R, NT = S::NT;
+    constexpr int DH = D / R;     // members of a row this thread handles
+    constexpr int OH = NHW / R;   // outputs of an output half this thread finishes
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sW = base;                                              // W digits (1024-aligned)
     double2 *stg = reinterpret_cast<double2 *>(sW + S::WBYTES);      // [member][row]
-    int *sE = reinterpret_cast<int *>(stg + 128 * D);                // [half][row] partial exponents
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sE + 256);
+    int *sE = reinterpret_cast<int *>(stg + 128 * D);                // [part][row] partial exponents
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sE + NT);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid & 127, half = tid >> 7;  // slice row = TMEM lane; members [half * DH, half * DH + DH)
+                                                 // (half: this thread's part of the row, 0..R-1)
 
-    for (int i = tid; i < S::WBYTES / 16; i += 256)
+    for (int i = tid; i < S::WBYTES / 16; i += NT)
         reinterpret_cast<uint4 *>(sW)[i] = __ldg(reinterpret_cast<const uint4 *>(wimg) + i);
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
@@ -189,7 +196,9 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         }
         sE[half * 128 + row] = eh;
         __syncthreads();
-        const int er = max(sE[row], sE[128 + row]);
+        int er = sE[row];
+#pragma unroll
+        for (int r = 1; r < R; r++) er = max(er, sE[r * 128 + row]);
         // ---- digits of this thread's members, in chunks of (up to) 8 members
         constexpr int CH = DH < 8 ? DH : 8;
 #pragma unroll
@@ -392,14 +401,14 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     Targets tg;
     for (int i = 0; i < CAST_MAX_K; i++) tg.q[i] = i < K ? g.q[i] : 0;
     const uint64_t ntiles = uint64_t(1) << (sv->n - K - 7);
-    const size_t smem = 1024 + S::WBYTES + S::SBYTES + 256 * 4 + 64;
+    const size_t smem = 1024 + S::WBYTES + S::SBYTES + S::NT * 4 + 64;
     CAST_CUDA(cudaFuncSetAttribute(k_dense_oz<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int per_sm = 512 / S::NCOL;
     const uint64_t cap = uint64_t(sm_count_cached()) * per_sm;
     const uint64_t grid = ntiles < cap ? ntiles : cap;
     const double N = double(uint64_t(1) << sv->n);
     ProfScope ps(sv->stream, "ozdense_k" + std::to_string(K) + "_c128", 32.0 * N, 8.0 * N * double(D));
-    k_dense_oz<K><<<(unsigned)grid, 256, smem, sv->stream>>>(reinterpret_cast<double2 *>(sv->data), ntiles, tg,
+    k_dense_oz<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<double2 *>(sv->data), ntiles, tg,
                                                              static_cast<const uint8_t *>(dev), P, kOzWait);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;

@@ -448,11 +448,16 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g) {
         return g.k == 4 || g.k >= 6 || 4 * ops <= 3 * dense_opcount(g.k);
     }
     // complex64: unitary gates of k >= 4 run on the tensor cores at about one
-    // memory pass (measured faster than the list at every density); other
-    // dense-class gates (non-unitary, or with the tensor cores off) on the
-    // CUDA cores, where the list kernel wins from k = 5 on and for sparse k = 4
+    // memory pass (measured faster than the list at every density).  Other
+    // dense-class gates (non-unitary, or with the tensor cores off) run on the
+    // CUDA cores; measured per 30-qubit gate, the list kernel beats the dense
+    // FP32 kernels for k = 5 up to ~80% of the dense operation count (15.6 ms
+    // dense vs 12.8-15.9), for k = 6, 7 up to ~40% (74 / 145 ms dense vs
+    // 32 / 61 ms), and for k = 4 up to 24 operations per amplitude
     if (tensor_mode_tf32x3() && g.unitary && g.k >= 4) return false;
-    return g.k >= 5 || (g.k == 4 && (ops >> g.k) <= 24);
+    if (g.k == 4) return (ops >> g.k) <= 24;
+    if (g.k == 5) return 5 * ops <= 4 * dense_opcount(g.k);
+    return g.k >= 6 && 5 * ops <= 2 * dense_opcount(g.k);
 }
 
 cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g) {

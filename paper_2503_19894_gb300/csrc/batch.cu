@@ -8,23 +8,27 @@
 // amplitudes).  Gate step s applies the s-th gate of every instance that has
 // one, in a single launch whose work items are the slices of all those
 // instances (an entry table per step: first work item, state offset, qubits,
-// matrix slot, parameter); a work item finds its entry by binary search.
+// matrix slot, parameter); each CTA takes a contiguous range of work items,
+// so a thread finds its entry once and then steps forward.
 // Rotation matrices are formed on the device from the parameters at the start
 // of every replay, so the whole launch sequence (initial states, gate steps,
 // energies; for gradients also lambda = H psi and the backward sweep) is
 // captured once into a CUDA graph and replayed per parameter set.
 //
 // Energies: one pass over every instance's amplitudes, each thread summing
-// c_t Re(conj(psi[x ^ xm_t]) phase_t(x) psi[x]) over its instance's terms in
-// FP64; warps add into the instance's slot with FP64 atomics.  Gradients:
-// lambda = H psi, then steps in reverse; a step forms Im<lambda|P_q|psi> for
-// every rotation in it (the derivative of exp(-i theta P / 2), accumulated in
-// FP64 into the parameter's slot) and un-applies each gate from psi and lambda
-// in the same pass.
+// c_t Re(conj(psi[x ^ xm_t]) i^q psi[x]) over its instance's terms (the Pauli
+// phase as a quarter-turn count q); warps add into the instance's FP64 slot.
+// Gradients: lambda = H psi, then steps in reverse; a step forms
+// Im<lambda|P_q|psi> for every rotation in it (the derivative of
+// exp(-i theta P / 2)) and un-applies each gate from psi and lambda in the same
+// pass; a thread's share for one parameter is summed in the state's
+// arithmetic and added to the parameter's FP64 slot once.
 //
-// complex64 runs in FP32 (products summed per thread in FP32, per-slice sums
-// in FP64); complex128 in double-float arithmetic on the FP32 pipe
-// (df64.cuh), the arena holding FP64 amplitudes.
+// complex64 runs in FP32 (energy terms summed per thread in FP32, then FP64);
+// complex128 in double-float arithmetic on the FP32 pipe (df64.cuh), the
+// arena holding FP64 amplitudes, energies in FP64.  Matrices are converted to
+// the arithmetic's format once per call, so no FP64 instruction runs per gate
+// application.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,16 +63,32 @@ struct BEntry {
 struct BTerm {
     double c;
     uint64_t xm, zm;
+    float ch, cl;  // c as a double-float pair (ch alone for complex64)
 };
 
-__device__ __forceinline__ int find_entry(const BEntry *e, int count, uint64_t w) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (e[mid].work0 <= w) lo = mid;
-        else hi = mid - 1;
+// Work distribution: CTA b takes the contiguous range [b c, b c + c) of the
+// work items (c a multiple of 32, so every warp's lanes run the same
+// iterations); a thread finds its first entry by binary search and then only
+// steps forward, since its items increase and entries are contiguous ranges.
+__device__ __forceinline__ void cta_range(uint64_t total, uint64_t &beg, uint64_t &end) {
+    const uint64_t c = ((total + gridDim.x - 1) / gridDim.x + 31) & ~uint64_t(31);
+    beg = uint64_t(blockIdx.x) * c;
+    end = beg + c < total ? beg + c : total;
+}
+
+template <class F>
+__device__ __forceinline__ int advance(int cur, uint64_t w, int count, F first_of) {
+    if (cur < 0) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first_of(mid) <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
     }
-    return lo;
+    while (cur + 1 < count && first_of(cur + 1) <= w) cur++;
+    return cur;
 }
 
 __device__ __forceinline__ uint64_t insert_zero(uint64_t t, int q) {
@@ -81,23 +101,33 @@ struct BA64 {
     using V = float2;
     __device__ static V in(Amp a) { return a; }
     __device__ static Amp out(V v) { return v; }
-    __device__ static V mul(double2 u, V x) {
-        const float ur = float(u.x), ui = float(u.y);
-        return make_float2(ur * x.x - ui * x.y, ur * x.y + ui * x.x);
-    }
+    using M = float2;  // matrix entry in the arithmetic's format
+    __device__ static M mat(double2 u) { return make_float2(float(u.x), float(u.y)); }
+    __device__ static V mulm(M u, V x) { return make_float2(u.x * x.x - u.y * x.y, u.x * x.y + u.y * x.x); }
+    __device__ static M conjm(M u) { return make_float2(u.x, -u.y); }
+    __device__ static bool nonzero(M u) { return u.x != 0.f || u.y != 0.f; }
     __device__ static V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
     __device__ static V zero() { return make_float2(0.f, 0.f); }
-    // conj(a) * b (re, im) for the gradient sums; converted once per slice
-    __device__ static double2 cdot(V a, V b) {
-        return make_double2(double(a.x * b.x + a.y * b.y), double(a.x * b.y - a.y * b.x));
-    }
-    __device__ static V scale(V a, double2 c) { return mul(c, a); }
-    // energies: c Re(ph conj(a) b) summed per thread in FP32, then once to FP64
+    // energies: c Re(i^q conj(a) b) summed per thread in FP32, then once to FP64
     using Acc = float;
-    __device__ static float term(Amp a, Amp b, double2 ph, double c) {
+    __device__ static float term(Amp a, Amp b, int q, const BTerm &T) {
         const float dr = a.x * b.x + a.y * b.y, di = a.x * b.y - a.y * b.x;
-        return float(c) * (float(ph.x) * dr - float(ph.y) * di);
+        const float re = q == 0 ? dr : q == 1 ? -di : q == 2 ? -dr : di;
+        return T.ch * re;
     }
+    // acc += c i^q x
+    __device__ static void add_scaled(V &acc, V x, int q, const BTerm &T) {
+        const V r = q == 0 ? x : q == 1 ? make_float2(-x.y, x.x) : q == 2 ? make_float2(-x.x, -x.y) : make_float2(x.y, -x.x);
+        acc.x = fmaf(T.ch, r.x, acc.x);
+        acc.y = fmaf(T.ch, r.y, acc.y);
+    }
+    // gradient sums: Re and Im of conj(a) b
+    using G = float;
+    __device__ static void gzero(G &g) { g = 0.f; }
+    __device__ static void gadd(G &g, float sgn, V a, V b, bool imag) {
+        g += sgn * (imag ? (a.x * b.y - a.y * b.x) : (a.x * b.x + a.y * b.y));
+    }
+    __device__ static double gval(const G &g) { return double(g); }
 };
 
 struct BA128 {
@@ -109,11 +139,19 @@ struct BA128 {
         const float rh = float(u.x), ih = float(u.y);
         return {rh, float(u.x - double(rh)), ih, float(u.y - double(ih))};
     }
-    __device__ static V mul(double2 u, V x) {
+    using M = float4;  // (re hi, re lo, im hi, im lo)
+    __device__ static M mat(double2 u) {
+        const V c = cf(u);
+        return make_float4(c.rh, c.rl, c.ih, c.il);
+    }
+    __device__ static V mulm(M u, V x) {
         V acc = {0.f, 0.f, 0.f, 0.f};
-        df::cmac(acc, cf(u), x);
+        const V uc = {u.x, u.y, u.z, u.w};
+        df::cmac(acc, uc, x);
         return acc;
     }
+    __device__ static M conjm(M u) { return make_float4(u.x, u.y, -u.z, -u.w); }
+    __device__ static bool nonzero(M u) { return u.x != 0.f || u.z != 0.f; }
     __device__ static V add(V a, V b) {
         V r = a;
         auto two = [](float &sh, float &sl, float xh, float xl) {
@@ -127,18 +165,36 @@ struct BA128 {
         return r;
     }
     __device__ static V zero() { return {0.f, 0.f, 0.f, 0.f}; }
-    __device__ static double2 cdot(V a, V b) {
-        const double ar = double(a.rh) + double(a.rl), ai = double(a.ih) + double(a.il);
-        const double br = double(b.rh) + double(b.rl), bi = double(b.ih) + double(b.il);
-        return make_double2(ar * br + ai * bi, ar * bi - ai * br);
-    }
-    __device__ static V scale(V a, double2 c) { return mul(c, a); }
-    // energies in FP64 on the stored amplitudes
+    // energies in FP64 on the stored amplitudes (the reductions of the method
+    // stay FP64; one pass per call)
     using Acc = double;
-    __device__ static double term(Amp a, Amp b, double2 ph, double c) {
+    __device__ static double term(Amp a, Amp b, int q, const BTerm &T) {
         const double dr = a.x * b.x + a.y * b.y, di = a.x * b.y - a.y * b.x;
-        return c * (ph.x * dr - ph.y * di);
+        const double re = q == 0 ? dr : q == 1 ? -di : q == 2 ? -dr : di;
+        return T.c * re;
     }
+    // acc += c i^q x, in double-float
+    __device__ static void add_scaled(V &acc, V x, int q, const BTerm &T) {
+        const V r = q == 0 ? x : q == 1 ? V{-x.ih, -x.il, x.rh, x.rl} : q == 2 ? V{-x.rh, -x.rl, -x.ih, -x.il}
+                                                                        : V{x.ih, x.il, -x.rh, -x.rl};
+        df::mac(acc.rh, acc.rl, T.ch, T.cl, r.rh, r.rl);
+        df::mac(acc.ih, acc.il, T.ch, T.cl, r.ih, r.il);
+    }
+    // gradient sums in double-float: Re or Im of conj(a) b
+    struct G {
+        float h, l;
+    };
+    __device__ static void gzero(G &g) { g = {0.f, 0.f}; }
+    __device__ static void gadd(G &g, float sgn, V a, V b, bool imag) {
+        if (imag) {  // a.re b.im - a.im b.re
+            df::mac(g.h, g.l, sgn * a.rh, sgn * a.rl, b.ih, b.il);
+            df::msub(g.h, g.l, sgn * a.ih, sgn * a.il, b.rh, b.rl);
+        } else {     // a.re b.re + a.im b.im
+            df::mac(g.h, g.l, sgn * a.rh, sgn * a.rl, b.rh, b.rl);
+            df::mac(g.h, g.l, sgn * a.ih, sgn * a.il, b.ih, b.il);
+        }
+    }
+    __device__ static double gval(const G &g) { return double(g.h) + double(g.l); }
 };
 
 // ------------------------------------------------------------- kernels
@@ -168,9 +224,10 @@ __global__ void k_batch_set_zero_state(void *arena, int amp_bytes, const uint64_
     else reinterpret_cast<double2 *>(arena)[offs[i]] = make_double2(1.0, 0.0);
 }
 
-// u (row-major 2^k x 2^k) or its adjoint applied to slice amplitudes v
+// u (row-major 2^k x 2^k, entries in the arithmetic's format) or its adjoint
+// applied to slice amplitudes v
 template <class A>
-__device__ __forceinline__ void apply_small(const double2 *u, int k, bool adj, typename A::V (&v)[4]) {
+__device__ __forceinline__ void apply_small(const typename A::M *u, int k, bool adj, typename A::V (&v)[4]) {
     using V = typename A::V;
     const int d = 1 << k;
     V y[4];
@@ -181,16 +238,23 @@ __device__ __forceinline__ void apply_small(const double2 *u, int k, bool adj, t
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             if (c >= d) break;
-            double2 m = adj ? u[c * d + r] : u[r * d + c];
-            if (adj) m.y = -m.y;
-            if (m.x == 0.0 && m.y == 0.0) continue;
-            acc = A::add(acc, A::mul(m, v[c]));
+            const typename A::M m = adj ? A::conjm(u[c * d + r]) : u[r * d + c];
+            if (!A::nonzero(m)) continue;
+            acc = A::add(acc, A::mulm(m, v[c]));
         }
         y[r] = acc;
     }
 #pragma unroll
     for (int r = 0; r < 4; r++)
         if (r < d) v[r] = y[r];
+}
+
+// every slot's matrix in the arithmetic's format (once per replay, after the
+// rotations were formed)
+template <class A>
+__global__ void k_batch_convert(const double2 *mats, typename A::M *out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = A::mat(mats[i]);
 }
 
 template <class A>
@@ -214,10 +278,14 @@ __device__ __forceinline__ void slice_addr(const BEntry &e, uint64_t t, uint64_t
 template <class A>
 __global__ void __launch_bounds__(kBThreads)
 k_batch_gate(typename A::Amp *__restrict__ psi, const BEntry *__restrict__ entries, int count, uint64_t total,
-             const double2 *__restrict__ mats) {
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t w = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total; w += stride) {
-        const BEntry e = entries[find_entry(entries, count, w)];
+             const typename A::M *__restrict__ mats) {
+    uint64_t beg, end;
+    cta_range(total, beg, end);
+    int ei = -1;
+    auto first_of = [&](int i) { return entries[i].work0; };
+    for (uint64_t w = beg + threadIdx.x; w < end; w += blockDim.x) {
+        ei = advance(ei, w, count, first_of);
+        const BEntry e = entries[ei];
         uint64_t a[4];
         slice_addr<A>(e, w - e.work0, a);
         typename A::V v[4];
@@ -232,13 +300,9 @@ k_batch_gate(typename A::Amp *__restrict__ psi, const BEntry *__restrict__ entri
     }
 }
 
-__device__ __forceinline__ double2 pauli_phase(uint64_t x, uint64_t xm, uint64_t zm) {
-    // P|x> = i^ny (-1)^{popc(x & zm)} |x ^ xm>, ny = popc(xm & zm)
-    const int ny = __popcll(xm & zm) & 3;
-    const int sg = __popcll(x & zm) & 1;
-    double2 ph = ny == 0 ? make_double2(1, 0) : ny == 1 ? make_double2(0, 1) : ny == 2 ? make_double2(-1, 0) : make_double2(0, -1);
-    if (sg) ph = make_double2(-ph.x, -ph.y);
-    return ph;
+// P|x> = i^q |x ^ xm> with q = popc(xm & zm) + 2 popc(x & zm) (mod 4)
+__device__ __forceinline__ int pauli_quarter(uint64_t x, uint64_t xm, uint64_t zm) {
+    return (__popcll(xm & zm) + 2 * (__popcll(x & zm) & 1)) & 3;
 }
 
 // energies[i] += sum over instance i's amplitudes and terms.  The loop is
@@ -249,26 +313,24 @@ __global__ void __launch_bounds__(kBThreads)
 k_batch_energy(const typename A::Amp *__restrict__ psi, const uint64_t *__restrict__ amp0, const uint64_t *offs,
                const int *__restrict__ tbeg, const BTerm *__restrict__ terms, int ninst, uint64_t total,
                double *energies) {
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    uint64_t beg, end;
+    cta_range(total, beg, end);
     const int lane = threadIdx.x & 31;
-    for (uint64_t wb = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); wb < total; wb += stride) {
+    int cur = -1;
+    auto first_of = [&](int i) { return amp0[i]; };
+    for (uint64_t wb = beg + (threadIdx.x & ~31u); wb < end; wb += blockDim.x) {
         const uint64_t w = wb + lane;
-        const bool act = w < total;
+        const bool act = w < end;
         int lo = -1;
         typename A::Acc acc = 0;
         if (act) {
-            int l = 0, hi = ninst - 1;
-            while (l < hi) {
-                const int mid = (l + hi + 1) >> 1;
-                if (amp0[mid] <= w) l = mid;
-                else hi = mid - 1;
-            }
-            lo = l;
+            cur = advance(cur, w, ninst, first_of);
+            lo = cur;
             const uint64_t x = w - amp0[lo];
             const typename A::Amp px = psi[offs[lo] + x];
             for (int t = tbeg[lo]; t < tbeg[lo + 1]; t++) {
                 const BTerm T = terms[t];
-                acc += A::term(psi[offs[lo] + (x ^ T.xm)], px, pauli_phase(x, T.xm, T.zm), T.c);
+                acc += A::term(psi[offs[lo] + (x ^ T.xm)], px, pauli_quarter(x, T.xm, T.zm), T);
             }
         }
         double v = double(acc);
@@ -290,21 +352,18 @@ __global__ void __launch_bounds__(kBThreads)
 k_batch_hpsi(const typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ lam,
              const uint64_t *__restrict__ amp0, const uint64_t *offs, const int *__restrict__ tbeg,
              const BTerm *__restrict__ terms, int ninst, uint64_t total) {
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t w = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total; w += stride) {
-        int lo = 0, hi = ninst - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (amp0[mid] <= w) lo = mid;
-            else hi = mid - 1;
-        }
+    uint64_t beg, end;
+    cta_range(total, beg, end);
+    int lo = -1;
+    auto first_of = [&](int i) { return amp0[i]; };
+    for (uint64_t w = beg + threadIdx.x; w < end; w += blockDim.x) {
+        lo = advance(lo, w, ninst, first_of);
         const uint64_t y = w - amp0[lo];
         typename A::V acc = A::zero();
         for (int t = tbeg[lo]; t < tbeg[lo + 1]; t++) {
             const BTerm T = terms[t];
             const uint64_t x = y ^ T.xm;
-            const double2 ph = pauli_phase(x, T.xm, T.zm);
-            acc = A::add(acc, A::scale(A::in(psi[offs[lo] + x]), make_double2(T.c * ph.x, T.c * ph.y)));
+            A::add_scaled(acc, A::in(psi[offs[lo] + x]), pauli_quarter(x, T.xm, T.zm), T);
         }
         lam[offs[lo] + y] = A::out(acc);
     }
@@ -314,19 +373,27 @@ k_batch_hpsi(const typename A::Amp *__restrict__ psi, typename A::Amp *__restric
 template <class A>
 __global__ void __launch_bounds__(kBThreads)
 k_batch_back(typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ lam,
-             const BEntry *__restrict__ entries, int count, uint64_t total, const double2 *__restrict__ mats,
+             const BEntry *__restrict__ entries, int count, uint64_t total, const typename A::M *__restrict__ mats,
              double *grads) {
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (uint64_t wb = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); wb < total; wb += stride) {
-        const uint64_t w = wb + lane;
-        const bool act = w < total;
-        const int ei = act ? find_entry(entries, count, w) : -1;
-        double g = 0.0;
-        bool rot = false;
-        if (act) {
-        const BEntry e = entries[ei];
-        rot = e.kind != BK_FIXED;
+    uint64_t beg, end;
+    cta_range(total, beg, end);
+    int cur = -1, gparam = -1;
+    typename A::G g;
+    A::gzero(g);
+    auto first_of = [&](int i) { return entries[i].work0; };
+    // a thread's items run through few entries: its gradient share of the
+    // current entry is summed in the state's arithmetic and added to the
+    // parameter's FP64 slot when the entry changes
+    auto flush = [&]() {
+        if (gparam >= 0) atomicAdd(grads + gparam, A::gval(g));
+        A::gzero(g);
+        gparam = -1;
+    };
+    for (uint64_t w = beg + threadIdx.x; w < end; w += blockDim.x) {
+        const int prev = cur;
+        cur = advance(cur, w, count, first_of);
+        if (cur != prev) flush();
+        const BEntry e = entries[cur];
         uint64_t a[4];
         slice_addr<A>(e, w - e.work0, a);
         typename A::V v[4], l[4];
@@ -337,19 +404,18 @@ k_batch_back(typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ la
                 v[j] = A::in(psi[a[j]]);
                 l[j] = A::in(lam[a[j]]);
             }
-        if (e.kind != BK_FIXED) {  // 1-qubit rotation: <lam|P|psi> on the slice
-            double2 s;
-            if (e.kind == BK_RX) {
-                const double2 t0 = A::cdot(l[0], v[1]), t1 = A::cdot(l[1], v[0]);
-                s = make_double2(t0.x + t1.x, t0.y + t1.y);
-            } else if (e.kind == BK_RY) {  // Y|0> = i|1>, Y|1> = -i|0>
-                const double2 t0 = A::cdot(l[0], v[1]), t1 = A::cdot(l[1], v[0]);
-                s = make_double2(t0.y - t1.y, -t0.x + t1.x);  // -i t0 + i t1
-            } else {
-                const double2 t0 = A::cdot(l[0], v[0]), t1 = A::cdot(l[1], v[1]);
-                s = make_double2(t0.x - t1.x, t0.y - t1.y);
+        if (e.kind != BK_FIXED) {  // 1-qubit rotation: Im<lam|P|psi> on the slice
+            gparam = e.param;
+            if (e.kind == BK_RX) {         // Im(conj(l0) v1 + conj(l1) v0)
+                A::gadd(g, 1.f, l[0], v[1], true);
+                A::gadd(g, 1.f, l[1], v[0], true);
+            } else if (e.kind == BK_RY) {  // Y|0> = i|1>, Y|1> = -i|0>: -Re(conj(l0) v1) + Re(conj(l1) v0)
+                A::gadd(g, -1.f, l[0], v[1], false);
+                A::gadd(g, 1.f, l[1], v[0], false);
+            } else {                       // Im(conj(l0) v0 - conj(l1) v1)
+                A::gadd(g, 1.f, l[0], v[0], true);
+                A::gadd(g, -1.f, l[1], v[1], true);
             }
-            g = s.y;
         }
         apply_small<A>(mats + size_t(e.mat) * 16, e.k, true, v);
         apply_small<A>(mats + size_t(e.mat) * 16, e.k, true, l);
@@ -359,18 +425,8 @@ k_batch_back(typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ la
                 psi[a[j]] = A::out(v[j]);
                 lam[a[j]] = A::out(l[j]);
             }
-        }
-        // the warp's lanes usually share an entry: one atomic per warp then
-        const unsigned full = 0xffffffffu;
-        const int first = __shfl_sync(full, ei, 0);
-        if (__all_sync(full, !act || ei == first)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(full, g, o);
-            if (lane == 0 && rot) atomicAdd(grads + entries[first].param, g);
-        } else if (act && rot) {
-            atomicAdd(grads + entries[ei].param, g);
-        }
     }
+    flush();
 }
 
 }  // namespace
@@ -401,6 +457,7 @@ struct cast_batch {
     uint64_t *d_offs = nullptr, *d_amp0 = nullptr;
     int *d_nq = nullptr, *d_tbeg = nullptr;
     double2 *d_mats = nullptr;
+    void *d_mats_a = nullptr;  // the same matrices in the arithmetic's format
     double *d_params = nullptr, *d_energy = nullptr, *d_grads = nullptr;
     cudaGraphExec_t g_energy = nullptr, g_grad = nullptr;
 };
@@ -421,10 +478,14 @@ void queue_forward(cast_batch *b) {
     k_batch_set_zero_state<<<(b->ninst + 127) / 128, 128, 0, b->stream>>>(b->psi, int(sizeof(Amp)), b->d_offs, b->ninst);
     const int ne = int(b->entries.size());
     if (ne > 0) k_batch_prep<<<(ne + 127) / 128, 128, 0, b->stream>>>(b->d_entries, ne, b->d_params, b->d_mats);
+    const int nm = b->nmat * 16;
+    if (nm > 0)
+        k_batch_convert<A><<<(nm + 255) / 256, 256, 0, b->stream>>>(b->d_mats, static_cast<typename A::M *>(b->d_mats_a), nm);
+    const typename A::M *mats = static_cast<const typename A::M *>(b->d_mats_a);
     for (int s = 0; s < S; s++) {
         const int e0 = b->step_begin[s], cnt = b->step_begin[s + 1] - e0;
         k_batch_gate<A><<<grid_of(b->step_work[s]), kBThreads, 0, b->stream>>>(
-            reinterpret_cast<Amp *>(b->psi), b->d_entries + e0, cnt, b->step_work[s], b->d_mats);
+            reinterpret_cast<Amp *>(b->psi), b->d_entries + e0, cnt, b->step_work[s], mats);
     }
     cudaMemsetAsync(b->d_energy, 0, sizeof(double) * b->ninst, b->stream);
     k_batch_energy<A><<<grid_of(b->total_amps), kBThreads, 0, b->stream>>>(
@@ -444,7 +505,7 @@ void queue_backward(cast_batch *b) {
         const int e0 = b->step_begin[s], cnt = b->step_begin[s + 1] - e0;
         k_batch_back<A><<<grid_of(b->step_work[s]), kBThreads, 0, b->stream>>>(
             reinterpret_cast<Amp *>(b->psi), reinterpret_cast<Amp *>(b->lam), b->d_entries + e0, cnt,
-            b->step_work[s], b->d_mats, b->d_grads);
+            b->step_work[s], static_cast<const typename A::M *>(b->d_mats_a), b->d_grads);
     }
 }
 
@@ -479,7 +540,7 @@ void free_batch(cast_batch *b) {
     if (b->g_energy) cudaGraphExecDestroy(b->g_energy);
     if (b->g_grad) cudaGraphExecDestroy(b->g_grad);
     void *ptrs[] = {b->psi, b->lam, b->d_entries, b->d_terms, b->d_offs, b->d_amp0, b->d_nq, b->d_tbeg,
-                    b->d_mats, b->d_params, b->d_energy, b->d_grads};
+                    b->d_mats, b->d_mats_a, b->d_params, b->d_energy, b->d_grads};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -578,7 +639,11 @@ cast_status cast_batch_create(int n_instances, const cast_circuit *circuits, con
         maxg = std::max(maxg, c.n_gates);
         b->tbeg.push_back(int(b->terms.size()));
         for (int t = 0; t < hams[i].n_terms; t++)
-            b->terms.push_back({hams[i].coeffs[t], hams[i].x_masks[t], hams[i].z_masks[t]});
+        {
+            const double c = hams[i].coeffs[t];
+            const float ch = float(c);
+            b->terms.push_back({c, hams[i].x_masks[t], hams[i].z_masks[t], ch, float(c - double(ch))});
+        }
     }
     b->tbeg.push_back(int(b->terms.size()));
     b->amp0.push_back(a0);
@@ -644,6 +709,7 @@ cast_status cast_batch_create(int n_instances, const cast_circuit *circuits, con
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->d_nq), b->nq.size() * 4);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->d_tbeg), b->tbeg.size() * 4);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->d_mats), size_t(b->nmat) * 16 * sizeof(double2));
+    if (e == cudaSuccess) e = alloc(&b->d_mats_a, size_t(b->nmat) * 16 * 16);  // float4 covers both formats
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->d_params), size_t(b->nparams) * 8);
     if (e == cudaSuccess) e = alloc(reinterpret_cast<void **>(&b->d_energy), size_t(b->ninst) * 8);
     if (e == cudaSuccess && b->grad) e = alloc(reinterpret_cast<void **>(&b->d_grads), size_t(b->nparams) * 8);
