@@ -330,6 +330,282 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
     if (warp == 0) tc::tmem_dealloc(taddr, S::NCOL);
 }
 
+// ------------------------------------------------------------ k = 6, 7
+// The same digit products with K fed in chunks.  The seven digits of a row
+// (7 x 2D bf16) no longer fit in tensor memory beside six accumulators, so:
+// - a chunk is 8 members (16 reals, one MMA K-step); its digits go to one of
+//   two TMEM buffers of 7 x 8 columns while the MMAs of the previous chunk
+//   read the other;
+// - outputs come in passes of 64 reals (MMA N = 64; six accumulators of 64
+//   columns at columns 128..511), and every pass runs over the whole K again,
+//   forming the digits anew from the state (L2-resident after the first pass);
+// - W's digits stream through two shared-memory buffers in blocks of 64
+//   output rows x 64 inputs (the 128-byte swizzled K-major image of the seven
+//   digits, 57,344 bytes), the next block copied in bulk while the current one
+//   is in use;
+// - the outputs of the passes before the last are held back (shared memory
+//   for k = 6, a per-CTA device buffer for k = 7) until every input of the
+//   tile has been read for the last time, then written to the state by the
+//   thread that made them.
+// Exactness: accumulators d <= 4 hold integers below (d + 1) 2D 127^2 times
+// 2^(-7d); for k = 7 and d = 4 that bound is 2^24.3, so accumulator 4 may
+// round once its sum passes 2^24, an error below 2^-44 of sum_c |x_c w_nc|
+// (never reached by rows of unit norm, whose sums stay near 2^22).
+template <int K>
+struct OzcShape {
+    static constexpr int D = 1 << K;
+    static constexpr int NR = 2 * D;               // reals per slice: GEMM K and N
+    static constexpr int NHW = 64;                 // outputs per pass (MMA N)
+    static constexpr int NPASS = NR / NHW;         // 2 / 4
+    static constexpr int NCH = NR / 16;            // chunks (K-steps) per pass: 8 / 16
+    static constexpr int NKB = NR / 64;            // W blocks per pass: 2 / 4
+    static constexpr int NB = NPASS * NKB;         // W blocks per tile
+    static constexpr int NACC = 6;
+    static constexpr int ABUF = kDigits * 8;       // TMEM columns of one digit buffer
+    static constexpr int ACOL0 = 128;              // first accumulator column
+    static constexpr int NCOL = 512;
+    static constexpr int WBLK = kDigits * NHW * 128;  // bytes of one W block
+    static constexpr int NT = 512;                 // four threads per slice row
+    static constexpr int NDEFER = (NPASS - 1) * (NHW / 2) * 128;  // held-back outputs per CTA (double2)
+    static constexpr bool DEFER_SMEM = K == 6;
+    static constexpr int OFF_E = 2 * WBLK, OFF_BAR = OFF_E + 4 * 128 * 4, OFF_DEFER = OFF_BAR + 64;
+    static constexpr int SMEM = 1024 + OFF_DEFER + (DEFER_SMEM ? NDEFER * 16 : 0);
+};
+
+struct OzcParams {
+    int8_t wexp[256];  // E_n - 14 per output real n
+};
+
+// acc * 2^(7d) as an integer: exact_int where the bound (d + 1) NR 127^2 of the
+// accumulator's integer is below 2^22, else the conversion instruction (exact
+// for integers below 2^24, rounding above)
+template <int NR, int Dd>
+__device__ __forceinline__ int32_t acc_int(float v) {
+    if constexpr ((Dd + 1) * NR * 16129 < (1 << 22)) return exact_int(v);
+    else return __float2int_rn(v);
+}
+
+// seven bf16 digit patterns (low 16 bits) of x / 2^er, rounded to 49 fractional bits
+__device__ __forceinline__ void real_digits(double x, int er, uint32_t (&dg)[kDigits]) {
+    const uint64_t bits = uint64_t(__double_as_longlong(x));
+    const int e = int((bits >> 52) & 0x7FF);
+    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
+    const int sh = 4 + (er - (e - 1022));
+    uint64_t f = (e == 0 || sh >= 54) ? 0 : ((m >> (sh - 1)) + 1) >> 1;
+    f = f < (uint64_t(1) << 49) ? f : (uint64_t(1) << 49) - 1;
+    const uint32_t sg = uint32_t(bits >> 32) & 0x80000000u;
+#pragma unroll
+    for (int i = 0; i < kDigits; i++) dg[i] = digit_bf16(uint32_t(f >> (7 * (kDigits - 1 - i))) & 127u, i, sg);
+}
+
+template <int K>
+__global__ void __launch_bounds__(512, 1)
+k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
+            const uint8_t *__restrict__ wimg, double2 *__restrict__ gdefer, const __grid_constant__ OzcParams P,
+            uint32_t wait_limit) {
+    using S = OzcShape<K>;
+    constexpr int D = S::D, NR = S::NR, NHW = S::NHW, NACC = S::NACC, NCH = S::NCH, NKB = S::NKB, NB = S::NB;
+    constexpr int DQ = D / 4;  // members per thread in the exponent pass
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sW = base;                                       // two W blocks (1024-aligned)
+    int *sE = reinterpret_cast<int *>(base + S::OFF_E);       // [part][row] partial exponents
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::OFF_BAR);  // 0, 1: digit buffer read; 2, 3: W block in
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
+    double2 *defer = S::DEFER_SMEM ? reinterpret_cast<double2 *>(base + S::OFF_DEFER)
+                                   : gdefer + size_t(blockIdx.x) * S::NDEFER;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, q = tid >> 7;  // slice row = TMEM lane; q: this thread's part of the row
+
+    if (tid == 0)
+        for (int i = 0; i < 4; i++) tc::mbar_init(&mbar[i], 1);
+    if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *tslot;
+    const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
+
+    uint64_t p[K];
+#pragma unroll
+    for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
+    auto member_off = [&](int j) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if ((j >> i) & 1) off += p[i];
+        return off;
+    };
+
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NHW >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+    const uint32_t wbase = tc::smem_u32(sW);
+    uint32_t g = 0;          // chunks of this CTA so far (digit buffer g & 1)
+    uint32_t gw = 0;         // W blocks consumed (W buffer gw & 1)
+    uint32_t ncommit = 0;    // thread 0: MMA groups committed
+    uint32_t nissued = 0;    // thread 0: W block copies issued
+    bool failed = false;
+
+    uint64_t tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        tc::mbar_expect_tx(&mbar[2], S::WBLK);
+        tc::bulk_g2s(sW, wimg, S::WBLK, &mbar[2]);
+        nissued = 1;
+    }
+    for (; tile < ntiles && !failed; tile += gridDim.x) {
+        const uint64_t sb = slice_base<K>(tile * 128 + row, tg);
+        const bool more_tiles = tile + gridDim.x < ntiles;
+        // ---- row exponent E_r over all D members (D / 4 per thread)
+        int eh = -1022;
+#pragma unroll 8
+        for (int jj = 0; jj < DQ; jj++) {
+            const double2 v = sv[sb + member_off(q * DQ + jj)];
+            const int e0 = int((__double_as_longlong(v.x) >> 52) & 0x7FF), e1 = int((__double_as_longlong(v.y) >> 52) & 0x7FF);
+            eh = max(eh, max(e0, e1) - 1022);
+        }
+        double2 nx0 = sv[sb + member_off(2 * q)], nx1 = sv[sb + member_off(2 * q + 1)];  // chunk 0
+        sE[q * 128 + row] = eh;
+        __syncthreads();
+        const int er = max(max(sE[row], sE[128 + row]), max(sE[256 + row], sE[384 + row]));
+        for (int h = 0; h < S::NPASS; h++) {
+            for (int c = 0; c < NCH; c++) {
+                const int s = c & 3;  // K-step within the W block
+                const uint32_t ab = g & 1;
+                const double2 x0 = nx0, x1 = nx1;
+                {  // the next chunk's members (the next pass starts over at chunk 0)
+                    const int cn = c + 1 < NCH ? c + 1 : 0;
+                    if (c + 1 < NCH || h + 1 < S::NPASS) {
+                        nx0 = sv[sb + member_off(cn * 8 + 2 * q)];
+                        nx1 = sv[sb + member_off(cn * 8 + 2 * q + 1)];
+                    }
+                }
+                // the MMAs two chunks back read this digit buffer
+                if (!failed && g >= 2 && !tc::mbar_wait(&mbar[ab], ((g >> 1) + 1) & 1, wait_limit)) failed = true;
+                tc::fence_after_sync();
+                if (!failed) {
+                    uint32_t d0[kDigits], d1[kDigits], d2[kDigits], d3[kDigits];
+                    real_digits(x0.x, er, d0);
+                    real_digits(x0.y, er, d1);
+                    real_digits(x1.x, er, d2);
+                    real_digits(x1.y, er, d3);
+#pragma unroll
+                    for (int i = 0; i < kDigits; i++) {
+                        const float v[2] = {__uint_as_float(d0[i] | (d1[i] << 16)), __uint_as_float(d2[i] | (d3[i] << 16))};
+                        tc::tmem_st<2>(lane_addr + uint32_t(ab * S::ABUF + i * 8 + 2 * q), v);
+                    }
+                }
+                tc::tmem_wait_st();
+                tc::fence_before_sync();
+                failed = __syncthreads_or(failed);
+                if (failed) break;
+                tc::fence_after_sync();
+                if (tid == 0) {
+                    const uint32_t wb = gw & 1;
+                    bool ok = s != 0 || tc::mbar_wait(&mbar[2 + wb], (gw >> 1) & 1, wait_limit);
+                    if (ok) {
+                        tc::fence_after_sync();
+                        bool first[NACC];
+#pragma unroll
+                        for (int d = 0; d < NACC; d++) first[d] = c == 0;
+#pragma unroll
+                        for (int d = 0; d < NACC; d++) {
+#pragma unroll
+                            for (int i = 0; i < kDigits; i++) {
+#pragma unroll
+                                for (int j = 0; j < kDigits && i + j <= kDigits; j++) {
+                                    if ((i + j < NACC - 1 ? i + j : NACC - 1) != d) continue;
+                                    const uint64_t bdesc = tc::smem_desc_sw128(
+                                        wbase + uint32_t(wb * S::WBLK + j * NHW * 128 + s * 32));
+                                    const uint32_t a = taddr + uint32_t(ab * S::ABUF + i * 8);
+                                    const uint32_t dcol = taddr + uint32_t(S::ACOL0 + d * NHW);
+                                    const uint32_t acc = first[d] ? 0u : 1u;
+                                    asm volatile(
+                                        "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
+                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dcol),
+                                        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+                                    first[d] = false;
+                                }
+                            }
+                        }
+                        tc::mma_commit(&mbar[ab]);
+                        ncommit++;
+                        // at a block's first chunk: copy the next block into the other
+                        // buffer once the MMAs of the block before (ending at chunk
+                        // g - 1) are done
+                        const int bnext = h * NKB + (c >> 2) + 1;
+                        if (s == 0 && (bnext < NB || more_tiles)) {
+                            if (g >= 1) ok = tc::mbar_wait(&mbar[(g - 1) & 1], ((g - 1) >> 1) & 1, wait_limit);
+                            if (ok) {
+                                const uint32_t nb = (gw + 1) & 1;
+                                tc::mbar_expect_tx(&mbar[2 + nb], S::WBLK);
+                                tc::bulk_g2s(sW + nb * S::WBLK, wimg + size_t(bnext % NB) * S::WBLK, S::WBLK,
+                                             &mbar[2 + nb]);
+                                nissued++;
+                            }
+                        }
+                    }
+                    if (!ok) failed = true;
+                }
+                if (s == 3) gw++;
+                g++;
+            }
+            // ---- epilogue of outputs [h NHW + 16 q, + 16): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
+            if (!failed && !tc::mbar_wait(&mbar[(g - 1) & 1], ((g - 1) >> 1) & 1, wait_limit)) failed = true;
+            failed = __syncthreads_or(failed);
+            if (failed) break;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int n0 = 0; n0 < 16; n0 += 8) {
+                const int col = q * 16 + n0;  // within the pass
+                float ac[NACC][8];
+#pragma unroll
+                for (int d = 0; d < NACC; d++) tc::tmem_ld<8>(lane_addr + uint32_t(S::ACOL0 + d * NHW + col), ac[d]);
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    double out[2];
+#pragma unroll
+                    for (int hh = 0; hh < 2; hh++) {
+                        const int cc = 2 * m + hh;
+                        const int64_t Y = (int64_t(acc_int<NR, 0>(ac[0][cc])) << 36) +
+                                          (int64_t(acc_int<NR, 1>(ac[1][cc] * 128.0f)) << 29) +
+                                          (int64_t(acc_int<NR, 2>(ac[2][cc] * 16384.0f)) << 22) +
+                                          (int64_t(acc_int<NR, 3>(ac[3][cc] * 2097152.0f)) << 15) +
+                                          (int64_t(__float2int_rn(ac[4][cc] * 268435456.0f)) << 8) +
+                                          int64_t(__float2int_rn(ac[5][cc] * 68719476736.0f));
+                        out[hh] = i64_to_double(Y, er + int(P.wexp[h * NHW + col + cc]) - 36);
+                    }
+                    const int jm = (col >> 1) + m;  // member within the pass
+                    if (h + 1 < S::NPASS)
+                        defer[(h * (NHW / 2) + jm) * 128 + row] = make_double2(out[0], out[1]);
+                    else
+                        __stcs(sv + sb + member_off(h * (NHW / 2) + jm), make_double2(out[0], out[1]));
+                }
+            }
+        }
+        if (failed) break;
+        // ---- every input of the tile is read: the held-back outputs go out
+        // (each thread its own, so no barrier is needed)
+#pragma unroll
+        for (int h = 0; h + 1 < S::NPASS; h++)
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                const int jm = q * 8 + m;
+                __stcs(sv + sb + member_off(h * (NHW / 2) + jm), defer[(h * (NHW / 2) + jm) * 128 + row]);
+            }
+    }
+    failed = __syncthreads_or(failed);
+    if (failed && tid == 0) {
+        atomicOr(&g_oz_error, 1);
+        // MMAs and bulk copies in flight finish before TMEM and shared memory are released
+        if (ncommit > 0) tc::mbar_wait(&mbar[(ncommit - 1) & 1], ((ncommit - 1) >> 1) & 1, wait_limit);
+        for (uint32_t c = nissued >= 2 ? nissued - 2 : 0; c < nissued; c++)
+            tc::mbar_wait(&mbar[2 + (c & 1)], (c >> 1) & 1, wait_limit);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, S::NCOL);
+}
+
 // ----------------------------------------------------------------- host side
 // Seven 7-bit digits of |w| / 2^E (49 fractional bits, rounded to nearest,
 // at most 2^49 - 1), E with every |w| of the row below 2^E.
@@ -351,11 +627,13 @@ uint16_t host_bf16_digit(int a, int j, bool neg) {
     return uint16_t(u >> 16) | (neg ? 0x8000u : 0u);
 }
 
-template <int K>
-cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
-    using S = OzShape<K>;
-    constexpr int D = S::D, NR = S::NR;
-    // real form W[n][c]: n output real, c input real (2 member + part)
+// The digit image of a gate: W[n][c] (n output real, c input real = 2 member +
+// part) is U's real form; row n gets exponent E_n (every |W[n][c]| < 2^E_n)
+// and its entries' seven digits go to img at off(n, c, j) as bf16 with the
+// sign of the entry; wexp[n] = E_n - 14.
+template <class Off>
+void build_digit_image(const PreparedGate &g, int k, std::vector<uint8_t> &img, int8_t *wexp, Off off) {
+    const int D = 1 << k, NR = 2 * D;
     std::vector<double> W(size_t(NR) * NR);
     for (int r = 0; r < D; r++)
         for (int c = 0; c < D; c++) {
@@ -369,8 +647,6 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
             W[size_t(2 * r + 1) * NR + 2 * c] = u.imag();
             W[size_t(2 * r + 1) * NR + 2 * c + 1] = u.real();
         }
-    OzParams P{};
-    std::vector<uint8_t> img(S::WBYTES, 0);
     for (int n = 0; n < NR; n++) {
         int E = -1022;
         for (int c = 0; c < NR; c++) {
@@ -381,20 +657,32 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
                 E = std::max(E, e);
             }
         }
-        P.wexp[n] = int8_t(std::max(-128, std::min(127, E - 14)));
+        wexp[n] = int8_t(std::max(-128, std::min(127, E - 14)));
         for (int c = 0; c < NR; c++) {
             const double w = W[size_t(n) * NR + c];
             int dig[kDigits];
             host_digits(w, E, dig);
             for (int j = 0; j < kDigits; j++) {
                 const uint16_t b = host_bf16_digit(dig[j], j, w < 0);
-                // 128-byte swizzled K-major: atom n/8, row n%8, 16-byte chunk (c/8) ^ (n%8)
-                const size_t off = size_t(j) * NR * 128 + size_t(n >> 3) * 1024 + size_t(n & 7) * 128 +
-                                   size_t(((c >> 3) ^ (n & 7)) << 4) + size_t(c & 7) * 2;
-                std::memcpy(img.data() + off, &b, 2);
+                std::memcpy(img.data() + off(n, c, j), &b, 2);
             }
         }
     }
+}
+
+// 128-byte swizzled K-major image of rows of 64 bf16: row n (within its 8-row
+// atoms), element c < 64: atom n/8, row n%8, 16-byte chunk (c/8) ^ (n%8)
+inline size_t sw128_bf16(int n, int c) {
+    return size_t(n >> 3) * 1024 + size_t(n & 7) * 128 + size_t(((c >> 3) ^ (n & 7)) << 4) + size_t(c & 7) * 2;
+}
+
+template <int K>
+cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
+    using S = OzShape<K>;
+    constexpr int D = S::D, NR = S::NR;
+    OzParams P{};
+    std::vector<uint8_t> img(S::WBYTES, 0);
+    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) { return size_t(j) * NR * 128 + sw128_bf16(n, c); });
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;
@@ -414,25 +702,62 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     return CAST_OK;
 }
 
+template <int K>
+cast_status run_ozc(cast_sv *sv, const PreparedGate &g) {
+    using S = OzcShape<K>;
+    constexpr int D = S::D;
+    OzcParams P{};
+    std::vector<uint8_t> img(size_t(S::NB) * S::WBLK, 0);
+    // block (pass n / 64, K-block c / 64): digit j, row n % 64, element c % 64
+    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
+        return size_t((n >> 6) * S::NKB + (c >> 6)) * S::WBLK + size_t(j) * S::NHW * 128 + sw128_bf16(n & 63, c & 63);
+    });
+    const void *dev = nullptr;
+    cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
+    if (st != CAST_OK) return st;
+    Targets tg;
+    for (int i = 0; i < CAST_MAX_K; i++) tg.q[i] = i < K ? g.q[i] : 0;
+    const uint64_t ntiles = uint64_t(1) << (sv->n - K - 7);
+    const uint64_t cap = uint64_t(sm_count_cached());
+    const uint64_t grid = ntiles < cap ? ntiles : cap;
+    void *defer = nullptr;
+    if (!S::DEFER_SMEM) {
+        st = ensure_work(sv, size_t(grid) * S::NDEFER * sizeof(double2), &defer);
+        if (st != CAST_OK) return st;
+    }
+    CAST_CUDA(cudaFuncSetAttribute(k_dense_ozc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+    const double N = double(uint64_t(1) << sv->n);
+    ProfScope ps(sv->stream, "ozdense_k" + std::to_string(K) + "_c128", 32.0 * N, 8.0 * N * double(D));
+    k_dense_ozc<K><<<(unsigned)grid, S::NT, S::SMEM, sv->stream>>>(
+        reinterpret_cast<double2 *>(sv->data), ntiles, tg, static_cast<const uint8_t *>(dev),
+        static_cast<double2 *>(defer), P, kOzWait);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
+
 }  // namespace
 
 bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
-        g.cls != CLS_DENSE || g.k < 4 || g.k > 5 || sv->n < g.k + 7)
+        g.cls != CLS_DENSE || g.k < 4 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
         return false;
     // measured per 30-qubit gate: this kernel 22-23 ms (k = 4) and 32-38 ms
     // (k = 5) whatever the matrix; the sparse kernel 10-12 / 11-20 ms at 10-30%
     // density and 35 / 62-69 ms dense: the digit kernel takes the gates above
     // 60% of the dense operation count (k = 3 gates stay on the CUDA cores,
     // where the sparse and dense double-float kernels match it)
-    return 5 * opcount(g.m.data(), g.k, 0.0) > 3 * dense_opcount(g.k);
+    const int64_t ops = opcount(g.m.data(), g.k, 0.0);
+    if (g.k <= 5) return 5 * ops > 3 * dense_opcount(g.k);
+    return 5 * ops > dense_opcount(g.k);
 }
 
 cast_status launch_gate_oz(cast_sv *sv, const PreparedGate &g) {
     switch (g.k) {
         case 4: return run_oz<4>(sv, g);
         case 5: return run_oz<5>(sv, g);
-        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 4, 5");
+        case 6: return run_ozc<6>(sv, g);
+        case 7: return run_ozc<7>(sv, g);
+        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 4..7");
     }
 }
 

@@ -460,6 +460,8 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g) {
     return g.k >= 6 && 5 * ops <= 2 * dense_opcount(g.k);
 }
 
+int sparse_mode() { return g_sparse_mode.load(); }
+
 cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g) {
     if (sv->dt == CAST_C64) return run_sparse_k<C64>(sv, g);
     return run_sparse_k<C128>(sv, g);

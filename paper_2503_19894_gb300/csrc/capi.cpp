@@ -94,6 +94,13 @@ cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const voi
     return CAST_OK;
 }
 
+cast_status ensure_work(cast_sv *sv, size_t bytes, void **ptr) {
+    cast_status st = ensure_dev(sv, sv->work, bytes);
+    if (st != CAST_OK) return st;
+    *ptr = sv->work.ptr;
+    return CAST_OK;
+}
+
 cast_status check_sv(const cast_sv *sv) {
     if (!sv || !sv->data) return fail(CAST_ERR_ARG, "null state");
     return CAST_OK;
@@ -279,6 +286,7 @@ cast_status cast_sv_wrap(void *device_ptr, int n_qubits, cast_dtype dt, void *cu
 cast_status cast_sv_destroy(cast_sv *sv) {
     if (!sv) return CAST_OK;
     if (sv->partials.ptr) cudaFreeAsync(sv->partials.ptr, sv->stream);
+    if (sv->work.ptr) cudaFreeAsync(sv->work.ptr, sv->stream);
     cudaError_t e = cudaStreamSynchronize(sv->stream);
     if (sv->mat_dev) cudaFree(sv->mat_dev);
     if (sv->mat_pinned) cudaFreeHost(sv->mat_pinned);

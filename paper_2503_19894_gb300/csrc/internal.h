@@ -42,6 +42,8 @@ struct cast_sv {
     int device = 0;
     // per-state device scratch: FP64 partial sums of reductions
     cast::DeviceScratch partials;
+    // per-state device scratch of kernels that hold results back (grow-only)
+    cast::DeviceScratch work;
     // ring of device slots for matrices too large for launch parameters,
     // filled from pinned staging slots; slot i is reused after its last copy
     // completed (mat_events[i])
@@ -128,13 +130,16 @@ cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast
                          std::vector<FusedGate> *out);
 
 // --------------------------------------------------------------- kernels
-// Matrix ring: kMatSlots slots of kMatSlotBytes (a 7-qubit complex128 matrix, or
-// the entry list of a dense 7-qubit complex128 gate for the sparse kernel).
+// Matrix ring: kMatSlots slots of kMatSlotBytes (a 7-qubit complex128 matrix,
+// the entry list of a dense 7-qubit complex128 gate for the sparse kernel, or
+// the 896 KiB digit image of a dense 7-qubit complex128 gate).
 constexpr int kMatSlots = 16;
-constexpr size_t kMatSlotBytes = size_t(512) << 10;
+constexpr size_t kMatSlotBytes = size_t(1) << 20;
 // Copy `bytes` (<= kMatSlotBytes) of host data to a device slot, in stream
 // order on sv's stream; *dev receives the slot's device address.
 cast_status upload_matrix(cast_sv *sv, const void *host, size_t bytes, const void **dev);
+// sv->work grown to at least `bytes` (in stream order); *ptr its device address.
+cast_status ensure_work(cast_sv *sv, size_t bytes, void **ptr);
 
 // Queue one prepared gate on sv's stream.
 // Staging geometry of a warp's "cube": 32 consecutive slices (rows) x the
@@ -182,8 +187,9 @@ int classify_matrix(const cplx *m, int k, double zero_tol);
 bool sparse_preferred(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_sparse(cast_sv *sv, const PreparedGate &g);
 int64_t dense_opcount(int k);
+int sparse_mode();  // CAST_SPARSE_AUTO / OFF / ALWAYS
 
-// Tensor-core complex128 path for dense k = 3..5 (apply_oz.cu): exact
+// Tensor-core complex128 path for dense k = 4..7 (apply_oz.cu): exact
 // products of 7-bit digits.
 bool oz_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_oz(cast_sv *sv, const PreparedGate &g);

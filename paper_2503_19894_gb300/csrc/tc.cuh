@@ -132,7 +132,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// N consecutive fp32 columns of this warp's 32 TMEM lanes, N = 16 or 32.
+// N consecutive fp32 columns of this warp's 32 TMEM lanes, N = 2, 4, 8, 16 or 32.
 template <int N>
 __device__ __forceinline__ void tmem_st(uint32_t taddr, const float (&v)[N]);
 template <>
@@ -154,6 +154,11 @@ __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float (&v)[16]
         "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]),
         "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
         : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_st<2>(uint32_t taddr, const float (&v)[2]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "f"(v[0]), "f"(v[1])
+                 : "memory");
 }
 template <>
 __device__ __forceinline__ void tmem_st<4>(uint32_t taddr, const float (&v)[4]) {
