@@ -106,10 +106,33 @@ struct OzParams {
     int8_t wexp[64];  // E_n - 14 per output real n
 };
 
-// bf16 bit pattern of s * a * 2^(-7 i), a an integer in [0, 127]
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t a, int i, uint32_t sign) {
-    const float f = (__uint_as_float(0x4B000000u | a) - 8388608.0f) * __uint_as_float(uint32_t(127 - 7 * i) << 23);
-    return (__float_as_uint(f) >> 16) | (a ? (sign >> 16) : 0u);
+// x / 2^er rounded to 49 fractional bits, as a magnitude F < 2^49, and the
+// fp32 magic number +-2^23 carrying the sign of x
+struct Fixed49 {
+    uint64_t f;
+    uint32_t mg;
+};
+__device__ __forceinline__ Fixed49 fixed49(double x, int er) {
+    const uint64_t bits = uint64_t(__double_as_longlong(x));
+    const int e = int((bits >> 52) & 0x7FF);
+    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
+    const int sh = 4 + (er - (e - 1022));
+    // nearest (unbiased; truncation would shrink every product and the error
+    // would build up over a circuit); a value that rounds up to 2^er keeps
+    // the largest fraction below it
+    uint64_t f = (e == 0 || sh >= 54) ? 0 : ((m >> (sh - 1)) + 1) >> 1;
+    f = f < (uint64_t(1) << 49) ? f : (uint64_t(1) << 49) - 1;
+    return {f, (uint32_t(bits >> 32) & 0x80000000u) | 0x4B000000u};
+}
+// digit i of v as the float +-a_i 2^(-7i): +-(2^23 + a) - (+-2^23) = +-a
+// exactly, then an exact power-of-two scale; its top half is the bf16 digit
+__device__ __forceinline__ float digit_f(const Fixed49 &v, int i) {
+    const uint32_t a = uint32_t(v.f >> (7 * (kDigits - 1 - i))) & 127u;
+    return (__uint_as_float(v.mg | a) - __uint_as_float(v.mg)) * __uint_as_float(uint32_t(127 - 7 * i) << 23);
+}
+// two such floats as one TMEM column of bf16 (lo: a, hi: b)
+__device__ __forceinline__ float bf16_pair(float a, float b) {
+    return __uint_as_float(__byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632));
 }
 
 // integer value of an fp32 holding an exact integer of magnitude < 2^22
@@ -203,34 +226,18 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         constexpr int CH = DH < 8 ? DH : 8;
 #pragma unroll
         for (int c0 = 0; c0 < DH; c0 += CH) {
-            uint64_t F[2 * CH];  // fixed-point magnitudes, 49 fractional bits below 2^er
-            uint32_t sg[2 * CH];
+            Fixed49 F[2 * CH];
 #pragma unroll
             for (int c = 0; c < CH; c++) {
                 const double2 x = stg[(half * DH + c0 + c) * 128 + row];
-#pragma unroll
-                for (int part = 0; part < 2; part++) {
-                    const uint64_t bits = uint64_t(__double_as_longlong(part ? x.y : x.x));
-                    const int e = int((bits >> 52) & 0x7FF);
-                    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
-                    const int sh = 4 + (er - (e - 1022));
-                    // nearest 49-bit fraction (unbiased: truncation would shrink every
-                    // product and the error would build up over a circuit); a value
-                    // that rounds up to 2^er keeps the largest fraction below it
-                    const uint64_t f = (e == 0 || sh >= 54) ? 0 : ((m >> (sh - 1)) + 1) >> 1;
-                    F[2 * c + part] = f < (uint64_t(1) << 49) ? f : (uint64_t(1) << 49) - 1;
-                    sg[2 * c + part] = uint32_t(bits >> 32) & 0x80000000u;
-                }
+                F[2 * c] = fixed49(x.x, er);
+                F[2 * c + 1] = fixed49(x.y, er);
             }
 #pragma unroll
             for (int i = 0; i < kDigits; i++) {
                 float v[CH];
-                const int sh = 7 * (kDigits - 1 - i);
 #pragma unroll
-                for (int c = 0; c < CH; c++) {
-                    const uint32_t a0 = uint32_t(F[2 * c] >> sh) & 127u, a1 = uint32_t(F[2 * c + 1] >> sh) & 127u;
-                    v[c] = __uint_as_float(digit_bf16(a0, i, sg[2 * c]) | (digit_bf16(a1, i, sg[2 * c + 1]) << 16));
-                }
+                for (int c = 0; c < CH; c++) v[c] = bf16_pair(digit_f(F[2 * c], i), digit_f(F[2 * c + 1], i));
                 tc::tmem_st<CH>(lane_addr + uint32_t(i * S::DCOL + half * DH + c0), v);
             }
         }
@@ -347,6 +354,18 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 //   for k = 6, a per-CTA device buffer for k = 7) until every input of the
 //   tile has been read for the last time, then written to the state by the
 //   thread that made them.
+// Warp roles: sixteen worker warps (four threads per slice row) form digits
+// and run the epilogues; a seventeenth issues the MMAs and the W copies.
+// Hand-offs are mbarriers:
+//   full[b]   digits of the chunk in buffer b stored (512 arrivals)   phase: chunk / 2
+//   free[b]   MMAs of the chunk in buffer b done (commit)             phase: chunk / 2
+//   wfull[b]  W block in shared buffer b (bulk-copy bytes)            phase: block / 2
+//   accfree   accumulators read by a pass's epilogue (512 arrivals)   phase: pass
+// The row exponents of the next tile are gathered during the last pass of
+// the current one.  Every wait is bounded; a thread that gives up raises a
+// shared flag, the workers agree on it at the per-tile barrier (bar.red.or),
+// and the control thread lets MMAs and copies in flight land before TMEM and
+// shared memory are released.
 // Exactness: accumulators d <= 4 hold integers below (d + 1) 2D 127^2 times
 // 2^(-7d); for k = 7 and d = 4 that bound is 2^24.3, so accumulator 4 may
 // round once its sum passes 2^24, an error below 2^-44 of sum_c |x_c w_nc|
@@ -360,16 +379,19 @@ struct OzcShape {
     static constexpr int NCH = NR / 16;            // chunks (K-steps) per pass: 8 / 16
     static constexpr int NKB = NR / 64;            // W blocks per pass: 2 / 4
     static constexpr int NB = NPASS * NKB;         // W blocks per tile
+    static constexpr int DQ = D / 4;               // members per thread in the exponent gather (2 per chunk)
     static constexpr int NACC = 6;
     static constexpr int ABUF = kDigits * 8;       // TMEM columns of one digit buffer
     static constexpr int ACOL0 = 128;              // first accumulator column
     static constexpr int NCOL = 512;
     static constexpr int WBLK = kDigits * NHW * 128;  // bytes of one W block
-    static constexpr int NT = 512;                 // four threads per slice row
+    static constexpr int NW = 512;                 // worker threads: four per slice row
+    static constexpr int NT = NW + 32;             // and the control warp
     static constexpr int NDEFER = (NPASS - 1) * (NHW / 2) * 128;  // held-back outputs per CTA (double2)
     static constexpr bool DEFER_SMEM = K == 6;
-    static constexpr int OFF_E = 2 * WBLK, OFF_BAR = OFF_E + 4 * 128 * 4, OFF_DEFER = OFF_BAR + 64;
+    static constexpr int OFF_E = 2 * WBLK, OFF_BAR = OFF_E + 2 * NW * 4, OFF_DEFER = OFF_BAR + 128;
     static constexpr int SMEM = 1024 + OFF_DEFER + (DEFER_SMEM ? NDEFER * 16 : 0);
+    static_assert(DQ == 2 * NCH, "two exponent members per chunk");
 };
 
 struct OzcParams {
@@ -385,224 +407,255 @@ __device__ __forceinline__ int32_t acc_int(float v) {
     else return __float2int_rn(v);
 }
 
-// seven bf16 digit patterns (low 16 bits) of x / 2^er, rounded to 49 fractional bits
-__device__ __forceinline__ void real_digits(double x, int er, uint32_t (&dg)[kDigits]) {
-    const uint64_t bits = uint64_t(__double_as_longlong(x));
-    const int e = int((bits >> 52) & 0x7FF);
-    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);
-    const int sh = 4 + (er - (e - 1022));
-    uint64_t f = (e == 0 || sh >= 54) ? 0 : ((m >> (sh - 1)) + 1) >> 1;
-    f = f < (uint64_t(1) << 49) ? f : (uint64_t(1) << 49) - 1;
-    const uint32_t sg = uint32_t(bits >> 32) & 0x80000000u;
-#pragma unroll
-    for (int i = 0; i < kDigits; i++) dg[i] = digit_bf16(uint32_t(f >> (7 * (kDigits - 1 - i))) & 127u, i, sg);
+__device__ __forceinline__ void oz_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+// barrier 1 over the worker warps, returning the OR of their predicates
+__device__ __forceinline__ bool workers_sync_or(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\tbar.red.or.pred b, 1, %2, a;\n\tselp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(p)), "n"(512)
+        : "memory");
+    return r != 0;
 }
 
 template <int K>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(OzcShape<K>::NT, 1)
 k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
             const uint8_t *__restrict__ wimg, double2 *__restrict__ gdefer, const __grid_constant__ OzcParams P,
             uint32_t wait_limit) {
     using S = OzcShape<K>;
-    constexpr int D = S::D, NR = S::NR, NHW = S::NHW, NACC = S::NACC, NCH = S::NCH, NKB = S::NKB, NB = S::NB;
-    constexpr int DQ = D / 4;  // members per thread in the exponent pass
+    constexpr int NHW = S::NHW, NACC = S::NACC, NCH = S::NCH, NKB = S::NKB, NB = S::NB, NR = S::NR;
+    constexpr int DQ = S::DQ;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sW = base;                                       // two W blocks (1024-aligned)
-    int *sE = reinterpret_cast<int *>(base + S::OFF_E);       // [part][row] partial exponents
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + S::OFF_BAR);  // 0, 1: digit buffer read; 2, 3: W block in
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 4);
-    double2 *defer = S::DEFER_SMEM ? reinterpret_cast<double2 *>(base + S::OFF_DEFER)
-                                   : gdefer + size_t(blockIdx.x) * S::NDEFER;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & 127, q = tid >> 7;  // slice row = TMEM lane; q: this thread's part of the row
+    uint8_t *sW = base;                                        // two W blocks (1024-aligned)
+    int *sE = reinterpret_cast<int *>(base + S::OFF_E);        // [tile parity][part][row] partial exponents
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + S::OFF_BAR);
+    uint64_t *full = bar, *freeb = bar + 2, *wfull = bar + 4, *accfree = bar + 6;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
+    volatile int *fail = reinterpret_cast<volatile int *>(bar + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    if (tid == 0)
-        for (int i = 0; i < 4; i++) tc::mbar_init(&mbar[i], 1);
+    if (tid == 0) {
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&full[b], S::NW);
+            tc::mbar_init(&freeb[b], 1);
+            tc::mbar_init(&wfull[b], 1);
+        }
+        tc::mbar_init(accfree, S::NW);
+        *fail = 0;
+    }
     if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
-    const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
+    const uint64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint64_t njobs = my_tiles * S::NPASS * NCH;  // chunk j: local tile j / (NPASS NCH), pass (j / NCH) % NPASS
 
-    uint64_t p[K];
+    if (warp == S::NW / 32) {
+        // ---------------- control: MMA issue and W copies (one thread)
+        if (lane == 0) {
+            const uint32_t idesc =
+                (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NHW >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+            const uint32_t wbase = tc::smem_u32(sW);
+            uint32_t ncommit = 0, nissued = 0, nw = 0;  // MMA groups committed, W copies issued, W blocks used
+            if (njobs > 0) {
+                tc::mbar_expect_tx(&wfull[0], S::WBLK);
+                tc::bulk_g2s(sW, wimg, S::WBLK, &wfull[0]);
+                nissued = 1;
+            }
+            for (uint64_t j = 0; j < njobs; j++) {
+                if (*fail) break;
+                const int c = int(j % NCH), s = c & 3;
+                const uint64_t pj = j / NCH;  // pass, counted over the tiles
+                const int h = int(pj % S::NPASS);
+                const uint32_t ab = uint32_t(j & 1), wb = nw & 1;
+                bool ok = true;
+                // the previous pass's epilogue has read the accumulators
+                if (c == 0 && pj >= 1) ok = tc::mbar_wait(accfree, uint32_t(pj - 1) & 1u, wait_limit);
+                if (ok && s == 0) ok = tc::mbar_wait(&wfull[wb], (nw >> 1) & 1u, wait_limit);
+                if (ok) ok = tc::mbar_wait(&full[ab], uint32_t(j >> 1) & 1u, wait_limit);
+                if (!ok) {
+                    *fail = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                bool first[NACC];
 #pragma unroll
-    for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
-    auto member_off = [&](int j) {
-        uint64_t off = 0;
+                for (int d = 0; d < NACC; d++) first[d] = c == 0;
 #pragma unroll
-        for (int i = 0; i < K; i++)
-            if ((j >> i) & 1) off += p[i];
-        return off;
-    };
-
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NHW >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-    const uint32_t wbase = tc::smem_u32(sW);
-    uint32_t g = 0;          // chunks of this CTA so far (digit buffer g & 1)
-    uint32_t gw = 0;         // W blocks consumed (W buffer gw & 1)
-    uint32_t ncommit = 0;    // thread 0: MMA groups committed
-    uint32_t nissued = 0;    // thread 0: W block copies issued
-    bool failed = false;
-
-    uint64_t tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles) {
-        tc::mbar_expect_tx(&mbar[2], S::WBLK);
-        tc::bulk_g2s(sW, wimg, S::WBLK, &mbar[2]);
-        nissued = 1;
-    }
-    for (; tile < ntiles && !failed; tile += gridDim.x) {
-        const uint64_t sb = slice_base<K>(tile * 128 + row, tg);
-        const bool more_tiles = tile + gridDim.x < ntiles;
-        // ---- row exponent E_r over all D members (D / 4 per thread)
-        int eh = -1022;
-#pragma unroll 8
-        for (int jj = 0; jj < DQ; jj++) {
-            const double2 v = sv[sb + member_off(q * DQ + jj)];
-            const int e0 = int((__double_as_longlong(v.x) >> 52) & 0x7FF), e1 = int((__double_as_longlong(v.y) >> 52) & 0x7FF);
-            eh = max(eh, max(e0, e1) - 1022);
+                for (int d = 0; d < NACC; d++) {
+#pragma unroll
+                    for (int i = 0; i < kDigits; i++) {
+#pragma unroll
+                        for (int jd = 0; jd < kDigits && i + jd <= kDigits; jd++) {
+                            if ((i + jd < NACC - 1 ? i + jd : NACC - 1) != d) continue;
+                            const uint64_t bdesc =
+                                tc::smem_desc_sw128(wbase + uint32_t(wb * S::WBLK + jd * NHW * 128 + s * 32));
+                            const uint32_t a = taddr + uint32_t(ab * S::ABUF + i * 8);
+                            const uint32_t dcol = taddr + uint32_t(S::ACOL0 + d * NHW);
+                            const uint32_t acc = first[d] ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dcol),
+                                "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+                            first[d] = false;
+                        }
+                    }
+                }
+                tc::mma_commit(&freeb[ab]);
+                ncommit++;
+                // at a block's first chunk: copy the next block into the other
+                // buffer once the MMAs of the block before (ending at chunk j - 1) are done
+                const int bnext = h * NKB + (c >> 2) + 1;
+                if (s == 0 && (bnext < NB || j / (S::NPASS * NCH) + 1 < my_tiles)) {
+                    if (j >= 1 && !tc::mbar_wait(&freeb[(j - 1) & 1], uint32_t((j - 1) >> 1) & 1u, wait_limit)) {
+                        *fail = 1;
+                        break;
+                    }
+                    const uint32_t nb = (nw + 1) & 1;
+                    tc::mbar_expect_tx(&wfull[nb], S::WBLK);
+                    tc::bulk_g2s(sW + nb * S::WBLK, wimg + size_t(bnext % NB) * S::WBLK, S::WBLK, &wfull[nb]);
+                    nissued++;
+                }
+                if (s == 3) nw++;
+            }
+            if (*fail) {  // MMAs and copies in flight land before TMEM and shared memory go away
+                atomicOr(&g_oz_error, 1);
+                if (ncommit > 0) tc::mbar_wait(&freeb[(ncommit - 1) & 1], ((ncommit - 1) >> 1) & 1u, wait_limit);
+                for (uint32_t cp = nissued >= 2 ? nissued - 2 : 0; cp < nissued; cp++)
+                    tc::mbar_wait(&wfull[cp & 1], (cp >> 1) & 1u, wait_limit);
+            }
         }
-        double2 nx0 = sv[sb + member_off(2 * q)], nx1 = sv[sb + member_off(2 * q + 1)];  // chunk 0
-        sE[q * 128 + row] = eh;
-        __syncthreads();
-        const int er = max(max(sE[row], sE[128 + row]), max(sE[256 + row], sE[384 + row]));
-        for (int h = 0; h < S::NPASS; h++) {
-            for (int c = 0; c < NCH; c++) {
-                const int s = c & 3;  // K-step within the W block
-                const uint32_t ab = g & 1;
-                const double2 x0 = nx0, x1 = nx1;
-                {  // the next chunk's members (the next pass starts over at chunk 0)
-                    const int cn = c + 1 < NCH ? c + 1 : 0;
+    } else {
+        // ---------------- workers: four threads per slice row
+        const int row = tid & 127, q = tid >> 7;  // slice row = TMEM lane; q: this thread's part of the row
+        const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
+        double2 *defer = S::DEFER_SMEM ? reinterpret_cast<double2 *>(base + S::OFF_DEFER)
+                                       : gdefer + size_t(blockIdx.x) * S::NDEFER;
+        uint64_t p[K];
+#pragma unroll
+        for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
+        auto member_off = [&](int jm) {
+            uint64_t off = 0;
+#pragma unroll
+            for (int i = 0; i < K; i++)
+                if ((jm >> i) & 1) off += p[i];
+            return off;
+        };
+        auto exp_of = [](const double2 &v) {
+            const int e0 = int((__double_as_longlong(v.x) >> 52) & 0x7FF), e1 = int((__double_as_longlong(v.y) >> 52) & 0x7FF);
+            return max(e0, e1) - 1022;
+        };
+        uint64_t j = 0;  // chunks so far (digit buffer j & 1)
+        int eh = -1022;  // this thread's share of the row exponent of the current tile
+        if (my_tiles > 0) {
+            const uint64_t sb0 = slice_base<K>(uint64_t(blockIdx.x) * 128 + row, tg);
+#pragma unroll 8
+            for (int jj = 0; jj < DQ; jj++) eh = max(eh, exp_of(sv[sb0 + member_off(q * DQ + jj)]));
+        }
+        for (uint64_t lt = 0; lt < my_tiles; lt++) {
+            const uint64_t tile = uint64_t(blockIdx.x) + lt * gridDim.x;
+            const uint64_t sb = slice_base<K>(tile * 128 + row, tg);
+            const bool more = lt + 1 < my_tiles;
+            const uint64_t sbn = more ? slice_base<K>((tile + gridDim.x) * 128 + row, tg) : sb;
+            int *e_t = sE + int(lt & 1) * S::NW;
+            e_t[q * 128 + row] = eh;
+            if (workers_sync_or(*fail != 0)) break;  // agreed: every worker leaves here
+            const int er = max(max(e_t[row], e_t[128 + row]), max(e_t[256 + row], e_t[384 + row]));
+            int eh_next = -1022;
+            double2 nx0 = sv[sb + member_off(2 * q)], nx1 = sv[sb + member_off(2 * q + 1)];  // chunk 0
+            for (int h = 0; h < S::NPASS; h++) {
+                for (int c = 0; c < NCH; c++) {
+                    const uint32_t ab = uint32_t(j & 1);
+                    const double2 x0 = nx0, x1 = nx1;
+                    const int cn = c + 1 < NCH ? c + 1 : 0;  // the next chunk's members (next pass: chunk 0)
                     if (c + 1 < NCH || h + 1 < S::NPASS) {
                         nx0 = sv[sb + member_off(cn * 8 + 2 * q)];
                         nx1 = sv[sb + member_off(cn * 8 + 2 * q + 1)];
                     }
-                }
-                // the MMAs two chunks back read this digit buffer
-                if (!failed && g >= 2 && !tc::mbar_wait(&mbar[ab], ((g >> 1) + 1) & 1, wait_limit)) failed = true;
-                tc::fence_after_sync();
-                if (!failed) {
-                    uint32_t d0[kDigits], d1[kDigits], d2[kDigits], d3[kDigits];
-                    real_digits(x0.x, er, d0);
-                    real_digits(x0.y, er, d1);
-                    real_digits(x1.x, er, d2);
-                    real_digits(x1.y, er, d3);
+                    if (h + 1 == S::NPASS && more) {  // the next tile's exponents, two members per chunk
+                        eh_next = max(eh_next, exp_of(sv[sbn + member_off(q * DQ + 2 * c)]));
+                        eh_next = max(eh_next, exp_of(sv[sbn + member_off(q * DQ + 2 * c + 1)]));
+                    }
+                    // the MMAs two chunks back read this digit buffer
+                    if (!*fail && j >= 2 && !tc::mbar_wait(&freeb[ab], uint32_t((j >> 1) + 1) & 1u, wait_limit))
+                        *fail = 1;
+                    tc::fence_after_sync();
+                    if (!*fail) {
+                        const Fixed49 f0 = fixed49(x0.x, er), f1 = fixed49(x0.y, er), f2 = fixed49(x1.x, er),
+                                      f3 = fixed49(x1.y, er);
 #pragma unroll
-                    for (int i = 0; i < kDigits; i++) {
-                        const float v[2] = {__uint_as_float(d0[i] | (d1[i] << 16)), __uint_as_float(d2[i] | (d3[i] << 16))};
-                        tc::tmem_st<2>(lane_addr + uint32_t(ab * S::ABUF + i * 8 + 2 * q), v);
+                        for (int i = 0; i < kDigits; i++) {
+                            const float v[2] = {bf16_pair(digit_f(f0, i), digit_f(f1, i)),
+                                                bf16_pair(digit_f(f2, i), digit_f(f3, i))};
+                            tc::tmem_st<2>(lane_addr + uint32_t(ab * S::ABUF + i * 8 + 2 * q), v);
+                        }
+                    }
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    oz_arrive(&full[ab]);
+                    j++;
+                }
+                // ---- epilogue of outputs [h NHW + 16 q, + 16): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
+                if (!*fail && !tc::mbar_wait(&freeb[(j - 1) & 1], uint32_t((j - 1) >> 1) & 1u, wait_limit)) *fail = 1;
+                tc::fence_after_sync();
+                if (!*fail) {
+#pragma unroll
+                    for (int n0 = 0; n0 < 16; n0 += 4) {
+                        const int col = q * 16 + n0;  // within the pass
+                        float ac[NACC][4];
+#pragma unroll
+                        for (int d = 0; d < NACC; d++)
+                            tc::tmem_ld<4>(lane_addr + uint32_t(S::ACOL0 + d * NHW + col), ac[d]);
+#pragma unroll
+                        for (int m = 0; m < 2; m++) {
+                            double out[2];
+#pragma unroll
+                            for (int hh = 0; hh < 2; hh++) {
+                                const int cc = 2 * m + hh;
+                                const int64_t Y = (int64_t(acc_int<NR, 0>(ac[0][cc])) << 36) +
+                                                  (int64_t(acc_int<NR, 1>(ac[1][cc] * 128.0f)) << 29) +
+                                                  (int64_t(acc_int<NR, 2>(ac[2][cc] * 16384.0f)) << 22) +
+                                                  (int64_t(acc_int<NR, 3>(ac[3][cc] * 2097152.0f)) << 15) +
+                                                  (int64_t(__float2int_rn(ac[4][cc] * 268435456.0f)) << 8) +
+                                                  int64_t(__float2int_rn(ac[5][cc] * 68719476736.0f));
+                                out[hh] = i64_to_double(Y, er + int(P.wexp[h * NHW + col + cc]) - 36);
+                            }
+                            const int jm = (col >> 1) + m;  // member within the pass
+                            if (h + 1 < S::NPASS)
+                                defer[(h * (NHW / 2) + jm) * 128 + row] = make_double2(out[0], out[1]);
+                            else
+                                __stcs(sv + sb + member_off(h * (NHW / 2) + jm), make_double2(out[0], out[1]));
+                        }
                     }
                 }
-                tc::tmem_wait_st();
                 tc::fence_before_sync();
-                failed = __syncthreads_or(failed);
-                if (failed) break;
-                tc::fence_after_sync();
-                if (tid == 0) {
-                    const uint32_t wb = gw & 1;
-                    bool ok = s != 0 || tc::mbar_wait(&mbar[2 + wb], (gw >> 1) & 1, wait_limit);
-                    if (ok) {
-                        tc::fence_after_sync();
-                        bool first[NACC];
-#pragma unroll
-                        for (int d = 0; d < NACC; d++) first[d] = c == 0;
-#pragma unroll
-                        for (int d = 0; d < NACC; d++) {
-#pragma unroll
-                            for (int i = 0; i < kDigits; i++) {
-#pragma unroll
-                                for (int j = 0; j < kDigits && i + j <= kDigits; j++) {
-                                    if ((i + j < NACC - 1 ? i + j : NACC - 1) != d) continue;
-                                    const uint64_t bdesc = tc::smem_desc_sw128(
-                                        wbase + uint32_t(wb * S::WBLK + j * NHW * 128 + s * 32));
-                                    const uint32_t a = taddr + uint32_t(ab * S::ABUF + i * 8);
-                                    const uint32_t dcol = taddr + uint32_t(S::ACOL0 + d * NHW);
-                                    const uint32_t acc = first[d] ? 0u : 1u;
-                                    asm volatile(
-                                        "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
-                                        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dcol),
-                                        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
-                                    first[d] = false;
-                                }
-                            }
-                        }
-                        tc::mma_commit(&mbar[ab]);
-                        ncommit++;
-                        // at a block's first chunk: copy the next block into the other
-                        // buffer once the MMAs of the block before (ending at chunk
-                        // g - 1) are done
-                        const int bnext = h * NKB + (c >> 2) + 1;
-                        if (s == 0 && (bnext < NB || more_tiles)) {
-                            if (g >= 1) ok = tc::mbar_wait(&mbar[(g - 1) & 1], ((g - 1) >> 1) & 1, wait_limit);
-                            if (ok) {
-                                const uint32_t nb = (gw + 1) & 1;
-                                tc::mbar_expect_tx(&mbar[2 + nb], S::WBLK);
-                                tc::bulk_g2s(sW + nb * S::WBLK, wimg + size_t(bnext % NB) * S::WBLK, S::WBLK,
-                                             &mbar[2 + nb]);
-                                nissued++;
-                            }
-                        }
-                    }
-                    if (!ok) failed = true;
-                }
-                if (s == 3) gw++;
-                g++;
+                oz_arrive(accfree);
             }
-            // ---- epilogue of outputs [h NHW + 16 q, + 16): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
-            if (!failed && !tc::mbar_wait(&mbar[(g - 1) & 1], ((g - 1) >> 1) & 1, wait_limit)) failed = true;
-            failed = __syncthreads_or(failed);
-            if (failed) break;
-            tc::fence_after_sync();
+            // ---- every input of the tile was read before the last chunk's digits
+            // went to the tensor cores: the held-back outputs go out (each thread
+            // its own, so no barrier is needed)
+            if (!*fail) {
 #pragma unroll
-            for (int n0 = 0; n0 < 16; n0 += 8) {
-                const int col = q * 16 + n0;  // within the pass
-                float ac[NACC][8];
+                for (int h = 0; h + 1 < S::NPASS; h++)
 #pragma unroll
-                for (int d = 0; d < NACC; d++) tc::tmem_ld<8>(lane_addr + uint32_t(S::ACOL0 + d * NHW + col), ac[d]);
-#pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    double out[2];
-#pragma unroll
-                    for (int hh = 0; hh < 2; hh++) {
-                        const int cc = 2 * m + hh;
-                        const int64_t Y = (int64_t(acc_int<NR, 0>(ac[0][cc])) << 36) +
-                                          (int64_t(acc_int<NR, 1>(ac[1][cc] * 128.0f)) << 29) +
-                                          (int64_t(acc_int<NR, 2>(ac[2][cc] * 16384.0f)) << 22) +
-                                          (int64_t(acc_int<NR, 3>(ac[3][cc] * 2097152.0f)) << 15) +
-                                          (int64_t(__float2int_rn(ac[4][cc] * 268435456.0f)) << 8) +
-                                          int64_t(__float2int_rn(ac[5][cc] * 68719476736.0f));
-                        out[hh] = i64_to_double(Y, er + int(P.wexp[h * NHW + col + cc]) - 36);
+                    for (int m = 0; m < 8; m++) {
+                        const int jm = q * 8 + m;
+                        __stcs(sv + sb + member_off(h * (NHW / 2) + jm), defer[(h * (NHW / 2) + jm) * 128 + row]);
                     }
-                    const int jm = (col >> 1) + m;  // member within the pass
-                    if (h + 1 < S::NPASS)
-                        defer[(h * (NHW / 2) + jm) * 128 + row] = make_double2(out[0], out[1]);
-                    else
-                        __stcs(sv + sb + member_off(h * (NHW / 2) + jm), make_double2(out[0], out[1]));
-                }
             }
+            eh = eh_next;
         }
-        if (failed) break;
-        // ---- every input of the tile is read: the held-back outputs go out
-        // (each thread its own, so no barrier is needed)
-#pragma unroll
-        for (int h = 0; h + 1 < S::NPASS; h++)
-#pragma unroll
-            for (int m = 0; m < 8; m++) {
-                const int jm = q * 8 + m;
-                __stcs(sv + sb + member_off(h * (NHW / 2) + jm), defer[(h * (NHW / 2) + jm) * 128 + row]);
-            }
-    }
-    failed = __syncthreads_or(failed);
-    if (failed && tid == 0) {
-        atomicOr(&g_oz_error, 1);
-        // MMAs and bulk copies in flight finish before TMEM and shared memory are released
-        if (ncommit > 0) tc::mbar_wait(&mbar[(ncommit - 1) & 1], ((ncommit - 1) >> 1) & 1, wait_limit);
-        for (uint32_t c = nissued >= 2 ? nissued - 2 : 0; c < nissued; c++)
-            tc::mbar_wait(&mbar[2 + (c & 1)], (c >> 1) & 1, wait_limit);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (tid == 0 && *fail) atomicOr(&g_oz_error, 1);
     if (warp == 0) tc::tmem_dealloc(taddr, S::NCOL);
 }
 
