@@ -344,16 +344,17 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 //   two TMEM buffers of 7 x 8 columns while the MMAs of the previous chunk
 //   read the other;
 // - outputs come in passes of 64 reals (MMA N = 64; six accumulators of 64
-//   columns at columns 128..511), and every pass runs over the whole K again,
-//   forming the digits anew from the state (L2-resident after the first pass);
+//   columns at columns 128..511), and every pass runs over the whole K again;
+//   pass 0 forms the digits from the state and also writes them to a per-CTA
+//   digit buffer in device memory (64 bytes per thread and chunk: 256 / 512
+//   KB per CTA for k = 6 / 7, meant to stay in L2), from which later passes
+//   reload them instead of forming them again;
 // - W's digits stream through two shared-memory buffers in blocks of 64
 //   output rows x 64 inputs (the 128-byte swizzled K-major image of the seven
 //   digits, 57,344 bytes), the next block copied in bulk while the current one
 //   is in use;
-// - the outputs of the passes before the last are held back (shared memory
-//   for k = 6, a per-CTA device buffer for k = 7) until every input of the
-//   tile has been read for the last time, then written to the state by the
-//   thread that made them.
+// - every read of a tile's state happens in pass 0, so each pass's outputs go
+//   straight back to the state after its epilogue.
 // Warp roles: sixteen worker warps (four threads per slice row) form digits
 // and run the epilogues; a seventeenth issues the MMAs and the W copies.
 // Hand-offs are mbarriers:
@@ -387,10 +388,11 @@ struct OzcShape {
     static constexpr int WBLK = kDigits * NHW * 128;  // bytes of one W block
     static constexpr int NW = 512;                 // worker threads: four per slice row
     static constexpr int NT = NW + 32;             // and the control warp
-    static constexpr int NDEFER = (NPASS - 1) * (NHW / 2) * 128;  // held-back outputs per CTA (double2)
-    static constexpr bool DEFER_SMEM = K == 6;
-    static constexpr int OFF_E = 2 * WBLK, OFF_BAR = OFF_E + 2 * NW * 4, OFF_DEFER = OFF_BAR + 128;
-    static constexpr int SMEM = 1024 + OFF_DEFER + (DEFER_SMEM ? NDEFER * 16 : 0);
+    // per-CTA digit buffer: a thread's seven bf16 pairs of a chunk (two columns
+    // each) padded to 64 bytes, [chunk][part][row]
+    static constexpr int NDIG = NCH * NW;  // uint4 x 4 entries per CTA
+    static constexpr int OFF_E = 2 * WBLK, OFF_BAR = OFF_E + 2 * NW * 4, OFF_OFF = OFF_BAR + 128;
+    static constexpr int SMEM = 1024 + OFF_OFF + D * 8;
     static_assert(DQ == 2 * NCH, "two exponent members per chunk");
 };
 
@@ -424,7 +426,7 @@ __device__ __forceinline__ bool workers_sync_or(bool p) {
 template <int K>
 __global__ void __launch_bounds__(OzcShape<K>::NT, 1)
 k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-            const uint8_t *__restrict__ wimg, double2 *__restrict__ gdefer, const __grid_constant__ OzcParams P,
+            const uint8_t *__restrict__ wimg, uint4 *__restrict__ gdig, const __grid_constant__ OzcParams P,
             uint32_t wait_limit) {
     using S = OzcShape<K>;
     constexpr int NHW = S::NHW, NACC = S::NACC, NCH = S::NCH, NKB = S::NKB, NB = S::NB, NR = S::NR;
@@ -437,7 +439,14 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
     uint64_t *full = bar, *freeb = bar + 2, *wfull = bar + 4, *accfree = bar + 6;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
     volatile int *fail = reinterpret_cast<volatile int *>(bar + 8);
+    uint64_t *sOff = reinterpret_cast<uint64_t *>(base + S::OFF_OFF);  // [member] offset in the state
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int jm = tid; jm < S::D; jm += S::NT) {
+        uint64_t off = 0;
+        for (int i = 0; i < K; i++)
+            if ((jm >> i) & 1) off += uint64_t(1) << tg.q[i];
+        sOff[jm] = off;
+    }
 
     if (tid == 0) {
         for (int b = 0; b < 2; b++) {
@@ -535,18 +544,9 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
         // ---------------- workers: four threads per slice row
         const int row = tid & 127, q = tid >> 7;  // slice row = TMEM lane; q: this thread's part of the row
         const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
-        double2 *defer = S::DEFER_SMEM ? reinterpret_cast<double2 *>(base + S::OFF_DEFER)
-                                       : gdefer + size_t(blockIdx.x) * S::NDEFER;
-        uint64_t p[K];
-#pragma unroll
-        for (int i = 0; i < K; i++) p[i] = uint64_t(1) << tg.q[i];
-        auto member_off = [&](int jm) {
-            uint64_t off = 0;
-#pragma unroll
-            for (int i = 0; i < K; i++)
-                if ((jm >> i) & 1) off += p[i];
-            return off;
-        };
+        uint4 *dig = gdig + size_t(blockIdx.x) * S::NDIG * 4 + size_t(tid) * 4;  // + chunk * NW * 4
+        // member offsets from the shared table (warp-uniform indices: broadcast reads)
+        auto member_off = [&](int jm) { return sOff[jm]; };
         auto exp_of = [](const double2 &v) {
             const int e0 = int((__double_as_longlong(v.x) >> 52) & 0x7FF), e1 = int((__double_as_longlong(v.y) >> 52) & 0x7FF);
             return max(e0, e1) - 1022;
@@ -568,50 +568,89 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
             if (workers_sync_or(*fail != 0)) break;  // agreed: every worker leaves here
             const int er = max(max(e_t[row], e_t[128 + row]), max(e_t[256 + row], e_t[384 + row]));
             int eh_next = -1022;
-            double2 nx0 = sv[sb + member_off(2 * q)], nx1 = sv[sb + member_off(2 * q + 1)];  // chunk 0
+            // inputs of the next chunk: pass 0 reads the state (last use: streaming
+            // loads), later passes the digits pass 0 left in the digit buffer
+            double2 nx0 = __ldcs(sv + sb + member_off(2 * q)), nx1 = __ldcs(sv + sb + member_off(2 * q + 1));
+            uint4 nd[4];
             for (int h = 0; h < S::NPASS; h++) {
                 for (int c = 0; c < NCH; c++) {
                     const uint32_t ab = uint32_t(j & 1);
                     const double2 x0 = nx0, x1 = nx1;
-                    const int cn = c + 1 < NCH ? c + 1 : 0;  // the next chunk's members (next pass: chunk 0)
-                    if (c + 1 < NCH || h + 1 < S::NPASS) {
-                        nx0 = sv[sb + member_off(cn * 8 + 2 * q)];
-                        nx1 = sv[sb + member_off(cn * 8 + 2 * q + 1)];
+                    uint4 dc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) dc[u] = nd[u];
+                    {
+                        const int cn = c + 1 < NCH ? c + 1 : 0, hn = c + 1 < NCH ? h : h + 1;
+                        if (hn == 0) {
+                            nx0 = __ldcs(sv + sb + member_off(cn * 8 + 2 * q));
+                            nx1 = __ldcs(sv + sb + member_off(cn * 8 + 2 * q + 1));
+                        } else if (hn < S::NPASS) {
+#pragma unroll
+                            for (int u = 0; u < 4; u++) nd[u] = dig[size_t(cn) * S::NW * 4 + u];
+                        }
                     }
-                    if (h + 1 == S::NPASS && more) {  // the next tile's exponents, two members per chunk
-                        eh_next = max(eh_next, exp_of(sv[sbn + member_off(q * DQ + 2 * c)]));
-                        eh_next = max(eh_next, exp_of(sv[sbn + member_off(q * DQ + 2 * c + 1)]));
+                    // the next tile's exponents, two members per chunk of the last pass
+                    // (used at the end of the chunk, so the loads overlap the digits)
+                    const bool gather = h + 1 == S::NPASS && more;
+                    double2 en0 = make_double2(0.0, 0.0), en1 = en0;
+                    if (gather) {
+                        en0 = sv[sbn + member_off(q * DQ + 2 * c)];
+                        en1 = sv[sbn + member_off(q * DQ + 2 * c + 1)];
                     }
                     // the MMAs two chunks back read this digit buffer
                     if (!*fail && j >= 2 && !tc::mbar_wait(&freeb[ab], uint32_t((j >> 1) + 1) & 1u, wait_limit))
                         *fail = 1;
                     tc::fence_after_sync();
                     if (!*fail) {
-                        const Fixed49 f0 = fixed49(x0.x, er), f1 = fixed49(x0.y, er), f2 = fixed49(x1.x, er),
-                                      f3 = fixed49(x1.y, er);
+                        float col[16];  // digit i: columns 2i, 2i + 1 (members 2q, 2q + 1)
+                        if (h == 0) {
+                            const Fixed49 f0 = fixed49(x0.x, er), f1 = fixed49(x0.y, er), f2 = fixed49(x1.x, er),
+                                          f3 = fixed49(x1.y, er);
+#pragma unroll
+                            for (int i = 0; i < kDigits; i++) {
+                                col[2 * i] = bf16_pair(digit_f(f0, i), digit_f(f1, i));
+                                col[2 * i + 1] = bf16_pair(digit_f(f2, i), digit_f(f3, i));
+                            }
+                            col[14] = col[15] = 0.f;
+#pragma unroll
+                            for (int u = 0; u < 4; u++)
+                                dig[size_t(c) * S::NW * 4 + u] =
+                                    make_uint4(__float_as_uint(col[4 * u]), __float_as_uint(col[4 * u + 1]),
+                                               __float_as_uint(col[4 * u + 2]), __float_as_uint(col[4 * u + 3]));
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                col[4 * u] = __uint_as_float(dc[u].x);
+                                col[4 * u + 1] = __uint_as_float(dc[u].y);
+                                col[4 * u + 2] = __uint_as_float(dc[u].z);
+                                col[4 * u + 3] = __uint_as_float(dc[u].w);
+                            }
+                        }
 #pragma unroll
                         for (int i = 0; i < kDigits; i++) {
-                            const float v[2] = {bf16_pair(digit_f(f0, i), digit_f(f1, i)),
-                                                bf16_pair(digit_f(f2, i), digit_f(f3, i))};
+                            const float v[2] = {col[2 * i], col[2 * i + 1]};
                             tc::tmem_st<2>(lane_addr + uint32_t(ab * S::ABUF + i * 8 + 2 * q), v);
                         }
                     }
                     tc::tmem_wait_st();
                     tc::fence_before_sync();
                     oz_arrive(&full[ab]);
+                    if (gather) eh_next = max(eh_next, max(exp_of(en0), exp_of(en1)));
                     j++;
                 }
-                // ---- epilogue of outputs [h NHW + 16 q, + 16): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
+                // ---- epilogue of outputs [h NHW + 16 q, + 16): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5).
+                // Every read of the tile's state happened in pass 0, before its last
+                // chunk's digits went to the tensor cores, so outputs go straight out.
                 if (!*fail && !tc::mbar_wait(&freeb[(j - 1) & 1], uint32_t((j - 1) >> 1) & 1u, wait_limit)) *fail = 1;
                 tc::fence_after_sync();
                 if (!*fail) {
 #pragma unroll
                     for (int n0 = 0; n0 < 16; n0 += 4) {
-                        const int col = q * 16 + n0;  // within the pass
+                        const int cl = q * 16 + n0;  // within the pass
                         float ac[NACC][4];
 #pragma unroll
                         for (int d = 0; d < NACC; d++)
-                            tc::tmem_ld<4>(lane_addr + uint32_t(S::ACOL0 + d * NHW + col), ac[d]);
+                            tc::tmem_ld<4>(lane_addr + uint32_t(S::ACOL0 + d * NHW + cl), ac[d]);
 #pragma unroll
                         for (int m = 0; m < 2; m++) {
                             double out[2];
@@ -624,30 +663,15 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
                                                   (int64_t(acc_int<NR, 3>(ac[3][cc] * 2097152.0f)) << 15) +
                                                   (int64_t(__float2int_rn(ac[4][cc] * 268435456.0f)) << 8) +
                                                   int64_t(__float2int_rn(ac[5][cc] * 68719476736.0f));
-                                out[hh] = i64_to_double(Y, er + int(P.wexp[h * NHW + col + cc]) - 36);
+                                out[hh] = i64_to_double(Y, er + int(P.wexp[h * NHW + cl + cc]) - 36);
                             }
-                            const int jm = (col >> 1) + m;  // member within the pass
-                            if (h + 1 < S::NPASS)
-                                defer[(h * (NHW / 2) + jm) * 128 + row] = make_double2(out[0], out[1]);
-                            else
-                                __stcs(sv + sb + member_off(h * (NHW / 2) + jm), make_double2(out[0], out[1]));
+                            const int jm = (cl >> 1) + m;  // member within the pass
+                            __stcs(sv + sb + member_off(h * (NHW / 2) + jm), make_double2(out[0], out[1]));
                         }
                     }
                 }
                 tc::fence_before_sync();
                 oz_arrive(accfree);
-            }
-            // ---- every input of the tile was read before the last chunk's digits
-            // went to the tensor cores: the held-back outputs go out (each thread
-            // its own, so no barrier is needed)
-            if (!*fail) {
-#pragma unroll
-                for (int h = 0; h + 1 < S::NPASS; h++)
-#pragma unroll
-                    for (int m = 0; m < 8; m++) {
-                        const int jm = q * 8 + m;
-                        __stcs(sv + sb + member_off(h * (NHW / 2) + jm), defer[(h * (NHW / 2) + jm) * 128 + row]);
-                    }
             }
             eh = eh_next;
         }
@@ -773,17 +797,15 @@ cast_status run_ozc(cast_sv *sv, const PreparedGate &g) {
     const uint64_t ntiles = uint64_t(1) << (sv->n - K - 7);
     const uint64_t cap = uint64_t(sm_count_cached());
     const uint64_t grid = ntiles < cap ? ntiles : cap;
-    void *defer = nullptr;
-    if (!S::DEFER_SMEM) {
-        st = ensure_work(sv, size_t(grid) * S::NDEFER * sizeof(double2), &defer);
-        if (st != CAST_OK) return st;
-    }
+    void *dig = nullptr;
+    st = ensure_work(sv, size_t(grid) * S::NDIG * 4 * sizeof(uint4), &dig);
+    if (st != CAST_OK) return st;
     CAST_CUDA(cudaFuncSetAttribute(k_dense_ozc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
     const double N = double(uint64_t(1) << sv->n);
     ProfScope ps(sv->stream, "ozdense_k" + std::to_string(K) + "_c128", 32.0 * N, 8.0 * N * double(D));
     k_dense_ozc<K><<<(unsigned)grid, S::NT, S::SMEM, sv->stream>>>(
         reinterpret_cast<double2 *>(sv->data), ntiles, tg, static_cast<const uint8_t *>(dev),
-        static_cast<double2 *>(defer), P, kOzWait);
+        static_cast<uint4 *>(dig), P, kOzWait);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
 }
