@@ -369,9 +369,9 @@ def verify_results(n, dtype, x, qft, rqc, max_k, zval, slices=16):
 
 def sweep_bench(n, mp, reps=8):
     """Dense Haar k-qubit gates, k = 1..7, on low / high / mixed targets, in
-    each arithmetic mode: GB/s per gate (2 x 2^n x S bytes), % of the measured
-    HBM peak and, on the tensor-core path, the executed 3xTF32 tensor flops
-    against the derived TF32 peak."""
+    each arithmetic mode, on a random state: GB/s per gate (2 x 2^n x S
+    bytes), % of the measured HBM peak and, on the tensor-core path, the
+    executed 3xTF32 tensor flops against the TF32 peak."""
     import torch
 
     import paper_2503_19894_gb300 as pkg
@@ -388,7 +388,10 @@ def sweep_bench(n, mp, reps=8):
         capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3 if mode == "tf32x3" else capi.CAST_TC_OFF)
         capi.cast_set_f64_mode(capi.CAST_F64_NATIVE if mode == "fp64" else capi.CAST_F64_EMULATED)
         S = 8 if dtype == "c64" else 16
-        sv = pkg.StateVector(n, dtype, init_index=W.random_basis_index(n, 5))
+        # a random state: the complex128 kernels are faster on zero amplitudes
+        sv = pkg.StateVector(n, dtype, init_index=None)
+        sv.tensor.copy_(W.random_state_device(n, dtype, 5))
+        torch.cuda.empty_cache()
         res = {}
         for k in range(1, 8):
             r = reps if (S == 8 or k <= 4) else 2

@@ -263,8 +263,8 @@ typedef struct {
     double zero_tol;       /* |real scalar| <= zero_tol counts as zero, default 1e-12 */
     int32_t amp_ops_per_pass; /* adaptive cost model: operations per amplitude that take as
                                  long as one pass over the state; 0 = measured default for
-                                 the state type (complex64: 82; complex128: 16 with
-                                 double-float arithmetic, 2 with native FP64) */
+                                 the state type (complex64: 82; complex128: 64 in the
+                                 emulated mode, 2 with native FP64) */
     const cast_cost_table *cost; /* adaptive: estimate a block by the measured time of its
                                     (size, class) instead of the operation-count model;
                                     with max_k = 0 the plan also picks the fusion width

@@ -30,6 +30,7 @@
 // of the slice adds 2^q[i] for every set bit i of j.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -541,7 +542,36 @@ __global__ void k_set_one(void *data, int dt, uint64_t index) {
         reinterpret_cast<double2 *>(data)[index] = make_double2(1.0, 0.0);
 }
 
+// Every amplitude a pseudo-random value with parts uniform in (-scale, scale)
+// (splitmix64 of the index; not normalised): a state on which the kernels'
+// value-dependent paths (zero rows, zero parts) behave as on a state in use.
+__global__ void k_fill_random(void *data, int dt, uint64_t N, uint64_t seed, float scale) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        // two signed 31-bit integers -> (-1, 1)
+        const float re = float(int32_t(uint32_t(z) >> 1) - (1 << 30)) * 0x1p-30f * scale;
+        const float im = float(int32_t(uint32_t(z >> 32) >> 1) - (1 << 30)) * 0x1p-30f * scale;
+        if (dt == CAST_C64)
+            reinterpret_cast<float2 *>(data)[i] = make_float2(re, im);
+        else
+            reinterpret_cast<double2 *>(data)[i] = make_double2(double(re), double(im));
+    }
+}
+
 }  // namespace
+
+cast_status launch_fill_random(cast_sv *sv, uint64_t seed) {
+    const uint64_t N = uint64_t(1) << sv->n;
+    const uint64_t cap = uint64_t(sm_count_cached()) * 8, need = (N + 255) / 256;
+    const float scale = std::ldexp(1.0f, -(sv->n + 1) / 2);
+    k_fill_random<<<(unsigned)(need < cap ? need : cap), 256, 0, sv->stream>>>(sv->data, sv->dt, N, seed, scale);
+    CAST_CUDA(cudaGetLastError());
+    return CAST_OK;
+}
 
 cast_status launch_set_one(cast_sv *sv, uint64_t index) {
     k_set_one<<<1, 1, 0, sv->stream>>>(sv->data, sv->dt, index);

@@ -234,11 +234,19 @@ struct Fuser {
 }  // namespace
 
 // Operations per amplitude that take as long as one pass over the state:
-// complex64 FP32 FMA 82; complex128 on double-float ~16 (each FMA costs about
-// ten FP32 instructions), on the FP64 pipe 2 (measured rates on GB300).
+// complex64 FP32 FMA 82; complex128 on the FP64 pipe 2 (measured rates on
+// GB300).  complex128 in the emulated mode runs dense gates of k >= 4 on the
+// tensor cores (digit products) and sparse ones on the list kernel: measured
+// on a random 30-qubit state, every gate of k <= 5 costs 1.5 to 6.3 passes
+// (7.7 ms diagonal, 13.2 ms dense k = 2, 24 ms dense k = 3, 4, 32 ms dense
+// k = 5) with no slope in the operation count the model could follow, and
+// merging pays almost always; 64 puts every gate of k <= 5 on the floor
+// P * 128, which reproduces the plans the measured cost table picks on the
+// six benchmark families (the 16 of the double-float CUDA-core kernels fused
+// too little: up to 1.6x slower than size-only).
 int64_t default_amp_ops_per_pass(cast_dtype dt) {
     if (dt == CAST_C64) return 82;
-    return f64_mode() == CAST_F64_EMULATED ? 16 : 2;
+    return f64_mode() == CAST_F64_EMULATED ? 64 : 2;
 }
 
 static cast_status fuse_once(const cast_circuit *c, const double *params, const cast_options *opt,

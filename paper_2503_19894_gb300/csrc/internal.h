@@ -212,6 +212,8 @@ int reduce_grid_blocks();
 size_t pauli_partials_needed(const PauliGroups &G);
 int sm_count_cached();
 cast_status launch_set_one(cast_sv *sv, uint64_t index);
+// Pseudo-random amplitudes of magnitude ~2^(-n/2) in every entry (timing probes).
+cast_status launch_fill_random(cast_sv *sv, uint64_t seed);
 cast_status launch_param_sum(cudaStream_t st, const double *gate_vals, const int *gate_pidx, int ngates,
                              double *grad, int nparams);
 cast_status launch_finalize(cudaStream_t st, const double *d_partials, int per_slot, int nslots,
