@@ -121,16 +121,18 @@ int cast_get_tensor_mode(void);
 
 /* complex128 dense gates on the tensor cores (process-wide setting):
  *   CAST_C128_TC_OFF: double-float arithmetic on the FP32 pipe;
- *   CAST_C128_TC_OZAKI (default): dense gates of k = 4, 5 on states of n >= k + 7
- *     qubits (in CAST_F64_EMULATED mode) as exact products of 7-bit digits
- *     on tcgen05 (kind::f16, bf16 operands, fp32 accumulation that never
- *     rounds for the three leading digit sums): each slice row and each row
- *     of the gate's real form is scaled by a power of two and cut to 49
- *     fractional bits (rounded), the digit-pair products with i + j <= 6
- *     are accumulated by weight, and the result is assembled with integer
- *     operations; error ~2^-46 of the slice's largest amplitude.  Gates with
- *     at most 60% of the dense operation count stay on the sparse kernel.  The paper has no tensor-core path; this is the complex128
- *     form of Eq. 3's matvec on GB300's tensor cores.
+ *   CAST_C128_TC_OZAKI (default): dense-class gates of k = 3..7 on states of
+ *     n >= k + 7 qubits (in CAST_F64_EMULATED mode) as exact products of
+ *     7-bit digits on tcgen05 (kind::f16, bf16 operands, fp32 accumulation
+ *     that never rounds for the five leading digit-weight sums): each slice
+ *     row and each row of the gate's real form is scaled by a power of two
+ *     and cut to 49 fractional bits (rounded), the digit-pair products with
+ *     i + j <= 7 are accumulated by weight, and the result is assembled with
+ *     integer operations; error ~2^-48 of the slice's largest amplitude.
+ *     Gates below about 50 / 33 / 40 / 10 / 5% of the dense operation count
+ *     (k = 3..7), where the list kernel is faster, stay on it.  The paper has
+ *     no tensor-core path; this is the complex128 form of Eq. 3's matvec on
+ *     GB300's tensor cores.
  * CAST_ERR_ARG for an unknown mode. */
 #define CAST_C128_TC_OFF 0
 #define CAST_C128_TC_OZAKI 1
@@ -145,9 +147,8 @@ int cast_get_c128_tensor_mode(void);
  * additions); entries within 1e-14 of +-1 or +-i count as exactly that value
  * (the paper's one tolerance).  Process-wide setting:
  *   CAST_SPARSE_AUTO (default): complex128 (double-float mode) gates of
- *     k = 4 (those the tensor-core digit kernel leaves), 6, 7, and of
- *     k = 3, 5 with at most 3/4 of the dense operation
- *     count; complex64 dense-class gates that the tensor cores do not take
+ *     k = 3..7 that the tensor-core digit kernels leave (every one with
+ *     CAST_C128_TC_OFF); complex64 dense-class gates that the tensor cores do not take
  *     (non-unitary, or tensor cores off) of k = 4 with at most 24
  *     operations per amplitude, k = 5 with at most 80% and k = 6, 7 with at
  *     most 40% of the dense operation count;

@@ -99,7 +99,7 @@ struct OzShape {
     // 256 columns, 64 registers), k = 5 one CTA of 16 warps (416 columns)
     static constexpr int R = 4;
     static constexpr int NT = 128 * R;
-    static constexpr int MIN_CTAS = K == 4 ? 2 : 1;
+    static constexpr int MIN_CTAS = K <= 4 ? 2 : 1;
 };
 
 struct OzParams {
@@ -814,25 +814,31 @@ cast_status run_ozc(cast_sv *sv, const PreparedGate &g) {
 
 bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
-        g.cls != CLS_DENSE || g.k < 4 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
+        g.cls != CLS_DENSE || g.k < 3 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
         return false;
-    // measured per 30-qubit gate: this kernel 22-23 ms (k = 4) and 32-38 ms
-    // (k = 5) whatever the matrix; the sparse kernel 10-12 / 11-20 ms at 10-30%
-    // density and 35 / 62-69 ms dense: the digit kernel takes the gates above
-    // 60% of the dense operation count (k = 3 gates stay on the CUDA cores,
-    // where the sparse and dense double-float kernels match it)
-    const int64_t ops = opcount(g.m.data(), g.k, 0.0);
-    if (g.k <= 5) return 5 * ops > 3 * dense_opcount(g.k);
-    return 5 * ops > dense_opcount(g.k);
+    // measured per 30-qubit gate on a random state: this kernel 18 / 20 / 31 /
+    // 28 / 49 ms (k = 3..7) whatever the matrix; the list kernel matches it at
+    // about 50 / 33 / 39 / 9.5 / 4.7% of the dense operation count (it is
+    // faster below, its time growing with the operation count above a floor
+    // of 15-44 ms)
+    const int64_t ops = opcount(g.m.data(), g.k, 0.0), dense = dense_opcount(g.k);
+    switch (g.k) {
+        case 3: return 2 * ops > dense;
+        case 4: return 3 * ops > dense;
+        case 5: return 5 * ops > 2 * dense;
+        case 6: return 10 * ops > dense;
+        default: return 20 * ops > dense;
+    }
 }
 
 cast_status launch_gate_oz(cast_sv *sv, const PreparedGate &g) {
     switch (g.k) {
+        case 3: return run_oz<3>(sv, g);
         case 4: return run_oz<4>(sv, g);
         case 5: return run_oz<5>(sv, g);
         case 6: return run_ozc<6>(sv, g);
         case 7: return run_ozc<7>(sv, g);
-        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 4..7");
+        default: return fail(CAST_ERR_UNSUPPORTED, "tensor-core complex128 path covers k = 3..7");
     }
 }
 

@@ -441,11 +441,12 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g) {
     if (mode == CAST_SPARSE_ALWAYS) return sv->dt == CAST_C64 || f64_mode() == CAST_F64_EMULATED;
     const int64_t ops = opcount(g.m.data(), g.k, 0.0);
     if (sv->dt == CAST_C128) {
-        if (f64_mode() != CAST_F64_EMULATED) return false;
-        // measured at 30 qubits: the list kernel beats the unrolled double-float
-        // one for every k = 4 gate and for k = 3, 5 gates up to 3/4 of the
-        // dense operation count; k = 6, 7 have no other double-float kernel
-        return g.k == 4 || g.k >= 6 || 4 * ops <= 3 * dense_opcount(g.k);
+        // measured on a random 30-qubit state: the list kernel is at least as
+        // fast as the unrolled double-float kernels for every dense-class gate of
+        // k >= 3 (dense k = 3: 25 vs 27 ms; k = 4: 39 vs 42 ms; k = 5: 70 vs 69
+        // ms), and k = 6, 7 have no other double-float kernel; the digit kernels
+        // (apply_oz.cu) take the denser gates before this test is reached
+        return f64_mode() == CAST_F64_EMULATED;
     }
     // complex64: unitary gates of k >= 4 run on the tensor cores at about one
     // memory pass (measured faster than the list at every density).  Other

@@ -1,6 +1,6 @@
 """complex128 dense gates on the tensor cores (7-bit digits, exact integer
 products; CAST_C128_TC_OZAKI) against the FP64 oracle: every target
-placement for k = 4..7 (k = 6, 7 on the K-chunked kernel), rows whose
+placement for k = 3..7 (k = 6, 7 on the K-chunked kernel), rows whose
 amplitudes span many orders of magnitude, digits at their largest, long gate
 sequences, fused circuits, full-size 30-qubit gates, and the kernel choice
 (profiled kernel families)."""
@@ -38,7 +38,7 @@ def run_gate(n, psi0, qubits, m):
     return out, [p["name"] for p in prof]
 
 
-@pytest.mark.parametrize("k", [4, 5, 6, 7])
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7])
 def test_oz_gate_every_placement(k, oz_mode):
     rng = np.random.default_rng(300 + k)
     for n in (k + 7, k + 8, 16):
@@ -53,7 +53,7 @@ def test_oz_gate_every_placement(k, oz_mode):
             assert rel_err(got, ref) <= 1e-13
 
 
-@pytest.mark.parametrize("k", [4, 5, 6, 7])
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7])
 def test_oz_rows_of_widely_spread_magnitudes(k, oz_mode):
     """Amplitudes from 1e-9 to 1 in one slice: the row exponent follows the
     largest, and the smallest still come out within the absolute bound."""
