@@ -271,9 +271,9 @@ def secondary_dtype(n, layers, max_k, dtype, steps=1, warmup=1, native_f64=False
     prof = capi.cast_profile_end()
     ms = e0.elapsed_time(e1) / steps
     if S == 16 and capi.cast_get_f64_mode() == capi.CAST_F64_EMULATED:
-        arith = "double-float on FP32"
+        arith = "double-float on FP32 (list kernel for sparse gates of k >= 3)"
         if capi.cast_get_c128_tensor_mode() == capi.CAST_C128_TC_OZAKI:
-            arith += "; dense k = 4, 5 as bf16 digit products on the tensor cores"
+            arith += "; denser gates of k = 3..7 as bf16 digit products on the tensor cores"
     else:
         arith = "native"
     sv.close()
