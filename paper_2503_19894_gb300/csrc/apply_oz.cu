@@ -409,6 +409,33 @@ __device__ __forceinline__ int32_t acc_int(float v) {
     else return __float2int_rn(v);
 }
 
+// Digit-buffer accesses with an L2 eviction policy: kept (evict_last) from the
+// write in pass 0 until the last pass reloads them (evict_first), so the
+// buffer competes well against the state streaming through L2.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_drop() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_l2hint(uint4 *a, const uint4 &v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ uint4 ld_l2hint(const uint4 *a, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(a), "l"(pol)
+                 : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void oz_arrive(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(mbar)) : "memory");
 }
@@ -545,6 +572,7 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
         const int row = tid & 127, q = tid >> 7;  // slice row = TMEM lane; q: this thread's part of the row
         const uint32_t lane_addr = taddr + (uint32_t(32 * (warp & 3)) << 16);
         uint4 *dig = gdig + size_t(blockIdx.x) * S::NDIG * 4 + size_t(tid) * 4;  // + chunk * NW * 4
+        const uint64_t keep = l2_policy_keep(), drop = l2_policy_drop();
         // member offsets from the shared table (warp-uniform indices: broadcast reads)
         auto member_off = [&](int jm) { return sOff[jm]; };
         auto exp_of = [](const double2 &v) {
@@ -585,8 +613,9 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
                             nx0 = __ldcs(sv + sb + member_off(cn * 8 + 2 * q));
                             nx1 = __ldcs(sv + sb + member_off(cn * 8 + 2 * q + 1));
                         } else if (hn < S::NPASS) {
+                            const uint64_t pol = hn + 1 < S::NPASS ? keep : drop;  // the last reload lets go
 #pragma unroll
-                            for (int u = 0; u < 4; u++) nd[u] = dig[size_t(cn) * S::NW * 4 + u];
+                            for (int u = 0; u < 4; u++) nd[u] = ld_l2hint(dig + size_t(cn) * S::NW * 4 + u, pol);
                         }
                     }
                     // the next tile's exponents, two members per chunk of the last pass
@@ -614,9 +643,10 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
                             col[14] = col[15] = 0.f;
 #pragma unroll
                             for (int u = 0; u < 4; u++)
-                                dig[size_t(c) * S::NW * 4 + u] =
-                                    make_uint4(__float_as_uint(col[4 * u]), __float_as_uint(col[4 * u + 1]),
-                                               __float_as_uint(col[4 * u + 2]), __float_as_uint(col[4 * u + 3]));
+                                st_l2hint(dig + size_t(c) * S::NW * 4 + u,
+                                          make_uint4(__float_as_uint(col[4 * u]), __float_as_uint(col[4 * u + 1]),
+                                                     __float_as_uint(col[4 * u + 2]), __float_as_uint(col[4 * u + 3])),
+                                          keep);
                         } else {
 #pragma unroll
                             for (int u = 0; u < 4; u++) {
