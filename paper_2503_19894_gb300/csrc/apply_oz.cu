@@ -1,4 +1,4 @@
-// Dense complex128 gates (k = 4, 5) on the tcgen05 tensor cores with an
+// Dense complex128 gates (k = 3..7) on the tcgen05 tensor cores with an
 // Ozaki-style split into exactly multiplied integer digits (Ozaki, Ogita and
 // Oishi 2012; Ootomo, Ozaki and Yokota 2024 for the GPU form).
 //
@@ -15,36 +15,41 @@
 // digits w_j.  Digits are stored pre-scaled, a_i 2^(-7i) and w_j 2^(-7j),
 // which bf16 represents exactly (7 significant bits times a power of two).
 //
-// Products.  For every pair (i, j) with i + j <= 7 one tcgen05.mma per
-// K-step (kind::f16, bf16 operands, fp32 accumulation; A = digit i of X from
-// tensor memory, B = digit j of W from shared memory) adds a_i w_j 2^(-7(i+j))
-// into accumulator min(i + j, 5).  Accumulators d = 0..4 only ever hold
-// integers times 2^(-7d) of magnitude below (d + 1) * 2D * 127^2 <= 5.2e6 <
-// 2^24 (in units of 2^(-7d)), so they are exact in fp32 whatever the order
-// of the additions or the rounding of the tensor cores; accumulator 5 gathers
-// the products of weight 2^-35 and below, where the fp32 accumulation
-// (it truncates, so its errors add up over the MMAs) costs about 2^-50 of
-// the output.  The dropped pairs (i + j >= 8) are all of the sign of their
-// product (every digit carries the sign of its value), so they shrink the
-// outputs by ~2^-53; with i + j <= 6 only, that bias was 2^-46 and the norm
-// of a state fell by 6.5e-12 over 200 gates.  Measured: a design that let
-// weights 2^-21 and below share one inexact accumulator was 3.5e-12 off, one
-// that let 2^-28 and below share it 1.8e-13 off (relative to the slice's
-// scale), against 1.5e-13 for a 2^-28 common integer scale alone: both limits
-// are gone here.
+// Products.  Every pair (i, j) with i + j <= 7 contributes a_i w_j
+// 2^(-7(i+j)) to accumulator d = i + j (eight accumulators, d = 0..7).  For a
+// fixed digit i of X the weights i + j of j = 0, 1, ... are consecutive, so
+// with the B blocks of W's digits stacked (rows of digit 0, then digit 1, ...)
+// and the accumulators in adjacent TMEM columns, one tcgen05.mma per (i,
+// K-step) (kind::f16, bf16 operands, fp32 accumulation; A = digit i of X from
+// tensor memory, B = the stacked digits of W from shared memory, N' = blocks x
+// N) adds all of digit i's pairs at once: 7 MMAs per K-step instead of 34.
+// The MMA of i = 0 also covers a zero eighth block, so it starts every
+// accumulator.  (Measured on GB300: an M = 128, K = 16 bf16 MMA costs ~53
+// cycles for any N <= 64, 69 at N = 128, 137 at N = 256.)  Accumulator d only
+// ever holds integers times 2^(-7d) of magnitude below (pairs of weight d) *
+// 2D * 127^2 <= 7 * 64 * 16129 < 2^23 (k <= 5), so all eight are exact in fp32
+// whatever the order of the additions or the rounding of the tensor cores.
+// The dropped pairs (i + j >= 8) are all of the sign of their product (every
+// digit carries the sign of its value), so they shrink the outputs by
+// ~2^-53; with i + j <= 6 only, that bias was 2^-46 and the norm of a state
+// fell by 6.5e-12 over 200 gates.  Measured: a design that let weights 2^-21
+// and below share one inexact accumulator was 3.5e-12 off, one that let
+// 2^-28 and below share it 1.8e-13 off (relative to the slice's scale),
+// against 1.5e-13 for a 2^-28 common integer scale alone: both limits are
+// gone here.
 //
-// Epilogue.  y = 2^(E_r + E_n - 14) (acc0 + ... + acc5): acc_d 2^(7d) for
+// Epilogue.  y = 2^(E_r + E_n - 14) (acc0 + ... + acc7): acc_d 2^(7d) for
 // d <= 3 are converted to integers exactly (fp32 magic-number rounding of an
-// exact integer below 2^22), acc4 * 2^28 (an exact integer below 2^24) and
-// acc5 * 2^36 are converted with rounding, the six are summed in 64-bit
-// integer arithmetic at the common scale 2^-36 and the result is written as
-// an FP64 with integer operations (leading-zero count, shift, exponent), so no
-// FP64 instruction runs on the device.
+// exact integer below 2^22), acc4 * 2^28 and acc5 * 2^36 (exact integers)
+// and acc6, acc7 * 2^36 (rounded) with the conversion instruction, the eight
+// are summed in 64-bit integer arithmetic at the common scale 2^-36 and the
+// result is written as an FP64 with integer operations (leading-zero count,
+// shift, exponent), so no FP64 instruction runs on the device.
 //
 // Tensor memory holds the seven digits of A (D columns each, two bf16 per
-// column) and six accumulators; for k = 4, 5 the outputs are produced in two
-// halves of D columns (MMAs of half the N, then that half's epilogue) so that
-// six accumulators fit beside the digits.
+// column) and the eight accumulators; for k = 4, 5 the outputs are produced
+// in two halves of D columns (MMAs of half the N, then that half's epilogue)
+// so that eight accumulators fit beside the digits.
 //
 // Data path: four threads per slice row (TMEM lane),
 // each with its share of the row's members.  A tile's 128 slice rows are
@@ -52,11 +57,11 @@
 // exponents meet in shared memory; each thread forms the digits of its members once per real
 // and stores them to tensor memory with tcgen05.st; one thread issues the MMAs and
 // commits them to an mbarrier; while they run, every thread loads the next
-// tile into shared memory; the epilogue reads the four accumulators with
+// tile into shared memory; the epilogue reads the eight accumulators with
 // tcgen05.ld and stores the outputs.  W's digits (host-built, already in the
 // 128-byte-swizzled K-major shared-memory image) are copied in once per CTA.
-// TMEM per CTA: 7 x D digit columns + 6 x 2D / NH accumulator columns (NH
-// output halves): 152 / 208 / 416 for k = 3 / 4 / 5, so 2 / 2 / 1 CTAs per SM.
+// TMEM per CTA: 7 x D digit columns + 8 x 2D / NH accumulator columns (NH
+// output halves): 184 / 240 / 480 for k = 3 / 4 / 5, so 2 / 2 / 1 CTAs per SM.
 // Waits on the mbarrier are bounded (error flag, no trap).
 #include <cuda_runtime.h>
 
@@ -89,11 +94,12 @@ struct OzShape {
     static constexpr int DCOL = NR / 2;      // TMEM columns of one digit (two bf16 per column)
     static constexpr int NH = K >= 4 ? 2 : 1;  // output halves (MMA N >= 16)
     static constexpr int NHW = NR / NH;        // outputs per half = MMA N
-    static constexpr int NACC = 6;
+    static constexpr int NACC = 8;                // one per digit weight d = i + j, 0..7
     static constexpr int ACOL0 = kDigits * DCOL;  // first accumulator column
     static constexpr int NCOL_USED = ACOL0 + NACC * NHW;
     static constexpr int NCOL = NCOL_USED <= 128 ? 128 : (NCOL_USED <= 256 ? 256 : 512);
-    static constexpr int WBYTES = kDigits * NR * 128;  // W digits: N rows of 128 bytes per digit
+    // W digits per output half: blocks j = 0..7 of NHW rows x 128 bytes (block 7 zero)
+    static constexpr int WBYTES = NH * NACC * NHW * 128;
     static constexpr int SBYTES = 128 * D * 16;        // staged tile: [member][row] double2
     // four threads per slice row: k = 4 two CTAs of 16 warps per SM (TMEM 2 x
     // 256 columns, 64 registers), k = 5 one CTA of 16 warps (416 columns)
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(OzShape<K>::NT, OzShape<K>::MIN_CTAS)
 k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
            const uint8_t *__restrict__ wimg, const __grid_constant__ OzParams P, uint32_t wait_limit) {
     using S = OzShape<K>;
-    constexpr int D = S::D, NR = S::NR, NHW = S::NHW, NACC = S::NACC;
+    constexpr int D = S::D, NHW = S::NHW, NACC = S::NACC;
     constexpr int R = S::R, NT = S::NT;
     constexpr int DH = D / R;     // members of a row this thread handles
     constexpr int OH = NHW / R;   // outputs of an output half this thread finishes
@@ -202,7 +208,8 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         }
     };
 
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NHW >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+    // kind::f16 with D fp32, A and B bf16, M = 128 (N set per MMA)
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(128 >> 4) << 24);
     const uint32_t wbase = tc::smem_u32(sW);
     uint32_t phase = 0;
     bool failed = false;
@@ -251,30 +258,25 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 #pragma unroll
         for (int h = 0; h < S::NH; h++) {
             if (tid == 0) {
-                bool first[NACC];
+                // one MMA per (A digit i, K-step): the B blocks of digits j = 0.. are
+                // stacked rows, and the accumulators of weights d = i + j adjacent
+                // columns, so N' = (blocks) x NHW covers accumulators i..7 at once.
+                // i = 0 also takes the zero block 7 and so starts every accumulator.
 #pragma unroll
-                for (int d = 0; d < NACC; d++) first[d] = true;
-#pragma unroll
-                for (int d = 0; d < NACC; d++) {
+                for (int ks = 0; ks < S::KS; ks++) {
 #pragma unroll
                     for (int i = 0; i < kDigits; i++) {
-#pragma unroll
-                        for (int j = 0; j < kDigits && i + j <= kDigits; j++) {
-                            if ((i + j < NACC - 1 ? i + j : NACC - 1) != d) continue;
-#pragma unroll
-                            for (int ks = 0; ks < S::KS; ks++) {
-                                const uint64_t bdesc =
-                                    tc::smem_desc_sw128(wbase + uint32_t(j * NR * 128 + h * NHW * 128 + ks * 32));
-                                const uint32_t a = taddr + uint32_t(i * S::DCOL + ks * 8);
-                                const uint32_t dcol = taddr + uint32_t(S::ACOL0 + d * NHW);
-                                const uint32_t acc = first[d] ? 0u : 1u;
-                                asm volatile(
-                                    "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
-                                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dcol),
-                                    "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
-                                first[d] = false;
-                            }
-                        }
+                        const int nblk = i == 0 ? NACC : NACC - i;
+                        const uint32_t idesc_i = idesc | (uint32_t((nblk * NHW) >> 3) << 17);
+                        const uint64_t bdesc =
+                            tc::smem_desc_sw128(wbase + uint32_t(h * NACC * NHW * 128 + ks * 32));
+                        const uint32_t a = taddr + uint32_t(i * S::DCOL + ks * 8);
+                        const uint32_t dcol = taddr + uint32_t(S::ACOL0 + i * NHW);
+                        const uint32_t acc = (ks == 0 && i == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dcol),
+                            "r"(a), "l"(bdesc), "r"(idesc_i), "r"(acc));
                     }
                 }
                 tc::mma_commit(mbar);
@@ -289,8 +291,8 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
             if (failed) break;
             phase ^= 1u;
             tc::fence_after_sync();
-            // ---- epilogue of outputs [h NHW + half OH, + OH): y = 2^(E_r + E_n - 14) (acc0 + ... + acc5)
-            constexpr int EC = OH < 16 ? OH : 16;
+            // ---- epilogue of outputs [h NHW + half OH, + OH): y = 2^(E_r + E_n - 14) (acc0 + ... + acc7)
+            constexpr int EC = OH < 4 ? OH : 4;
 #pragma unroll
             for (int n0 = 0; n0 < OH; n0 += EC) {
                 const int col = half * OH + n0;  // within this output half
@@ -303,13 +305,17 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 #pragma unroll
                     for (int hh = 0; hh < 2; hh++) {
                         const int c = 2 * m + hh;
-                        // common scale 2^-36 (in units of the weight-0 products)
+                        // common scale 2^-36 (in units of the weight-0 products): acc_d
+                        // 2^(7d) is an exact integer for every d; those of d <= 5 stay
+                        // exact at this scale, d = 6, 7 round to it
                         const int64_t Y = (int64_t(exact_int(ac[0][c])) << 36) +
                                           (int64_t(exact_int(ac[1][c] * 128.0f)) << 29) +
                                           (int64_t(exact_int(ac[2][c] * 16384.0f)) << 22) +
                                           (int64_t(exact_int(ac[3][c] * 2097152.0f)) << 15) +
                                           (int64_t(__float2int_rn(ac[4][c] * 268435456.0f)) << 8) +
-                                          int64_t(__float2int_rn(ac[5][c] * 68719476736.0f));
+                                          int64_t(__float2int_rn(ac[5][c] * 68719476736.0f)) +
+                                          int64_t(__float2int_rn(ac[6][c] * 68719476736.0f)) +
+                                          int64_t(__float2int_rn(ac[7][c] * 68719476736.0f));
                         out[hh] = i64_to_double(Y, er_cur + int(P.wexp[h * NHW + col + c]) - 36);
                     }
                     const int j = ((h * NHW + col) >> 1) + m;
@@ -786,10 +792,13 @@ inline size_t sw128_bf16(int n, int c) {
 template <int K>
 cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     using S = OzShape<K>;
-    constexpr int D = S::D, NR = S::NR;
+    constexpr int D = S::D;
     OzParams P{};
     std::vector<uint8_t> img(S::WBYTES, 0);
-    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) { return size_t(j) * NR * 128 + sw128_bf16(n, c); });
+    // half n / NHW, digit block j, row n % NHW (block 7 stays zero)
+    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
+        return (size_t(n / S::NHW) * S::NACC + size_t(j)) * S::NHW * 128 + sw128_bf16(n % S::NHW, c);
+    });
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;
