@@ -855,16 +855,16 @@ bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
         g.cls != CLS_DENSE || g.k < 3 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
         return false;
-    // measured per 30-qubit gate on a random state: this kernel 18 / 20 / 31 /
-    // 28 / 49 ms (k = 3..7) whatever the matrix; the list kernel matches it at
-    // about 50 / 33 / 39 / 9.5 / 4.7% of the dense operation count (it is
-    // faster below, its time growing with the operation count above a floor
-    // of 15-44 ms)
+    // measured per 30-qubit gate on a random state: this kernel 16.5-19 /
+    // 16.7-18.3 / 21-24 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the
+    // list kernel matches it at about 43 / 21 / 25 / 9.5 / 4.7% of the dense
+    // operation count (it is faster below, its time growing with the
+    // operation count above a floor of 15-44 ms)
     const int64_t ops = opcount(g.m.data(), g.k, 0.0), dense = dense_opcount(g.k);
     switch (g.k) {
-        case 3: return 2 * ops > dense;
-        case 4: return 3 * ops > dense;
-        case 5: return 5 * ops > 2 * dense;
+        case 3: return 7 * ops > 3 * dense;
+        case 4: return 9 * ops > 2 * dense;
+        case 5: return 4 * ops > dense;
         case 6: return 10 * ops > dense;
         default: return 20 * ops > dense;
     }
