@@ -469,14 +469,20 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
                      ("adaptive_k5", capi.options("adaptive", 5)),
                      ("adaptive_measured_k5", capi.options("adaptive", 5, cost=tables[dt])),
                      ("adaptive_measured_width_search", capi.options("adaptive", 0, cost=tables[dt])))
-            sv = pkg.StateVector(n, dt, init_index=W.random_basis_index(n, 1))
+            # every application starts from the same random state: the complex128
+            # kernels are faster on zero amplitudes, and a plan applied again and
+            # again to one state (QFT^4 = 1) would be timed on different contents
+            psi0 = W.random_state_device(n, dt, 1)
+            sv = pkg.StateVector(n, dt, init_index=None)
             res = {}
             for name, opts in modes:
                 h0 = time.perf_counter()
                 plan = capi.cast_plan_create(n, gates, opts=opts, dtype=dt)
                 host_ms = (time.perf_counter() - h0) * 1e3
                 count, ops = capi.cast_plan_info(plan)
+                sv.tensor.copy_(psi0)
                 capi.cast_plan_apply(sv.handle, plan)  # warm-up
+                sv.tensor.copy_(psi0)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -484,6 +490,7 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1)
+                sv.tensor.copy_(psi0)
                 capi.cast_profile_begin()  # per kernel family, one more application
                 capi.cast_plan_apply(sv.handle, plan)
                 prof = capi.cast_profile_end()
@@ -498,6 +505,7 @@ def fusion_ablation(n, families=None, dtypes=("c64", "c128")):
             res["adaptive_vs_size"] = round(res["adaptive_measured_width_search"]["device_ms"] /
                                             res["size_k5"]["device_ms"], 4)
             sv.close()
+            del psi0
             torch.cuda.empty_cache()
             fam_out[dt] = res
         out["families"][fam] = fam_out
