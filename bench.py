@@ -379,13 +379,17 @@ def sweep_bench(n, mp, reps=8):
     import oracle
     try:
         tf32, tsrc = capi.cast_measure_tensor_peak(capi.CAST_PEAK_TF32), "measured"
+        bf16 = capi.cast_measure_tensor_peak(capi.CAST_PEAK_BF16)
     except capi.CastError:
         tf32, tsrc = mp.get("bf16_tflops_sustained", 1739.5) * 1.1 / 2.25, "derived"
+        bf16 = mp.get("bf16_tflops", 1933.0)
     rng = np.random.default_rng(77)
     tc0, f640 = capi.cast_get_tensor_mode(), capi.cast_get_f64_mode()
     out = {}
-    for dtype, mode in (("c64", "fp32"), ("c64", "tf32x3"), ("c128", "double-float"), ("c128", "fp64")):
-        capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3 if mode == "tf32x3" else capi.CAST_TC_OFF)
+    for dtype, mode in (("c64", "fp32"), ("c64", "tf32x3"), ("c64", "bf16x6"), ("c128", "double-float"),
+                        ("c128", "fp64")):
+        capi.cast_set_tensor_mode({"tf32x3": capi.CAST_TC_TF32X3, "bf16x6": capi.CAST_TC_BF16X6}.get(
+            mode, capi.CAST_TC_OFF))
         capi.cast_set_f64_mode(capi.CAST_F64_NATIVE if mode == "fp64" else capi.CAST_F64_EMULATED)
         S = 8 if dtype == "c64" else 16
         # a random state: the complex128 kernels are faster on zero amplitudes
@@ -415,6 +419,9 @@ def sweep_bench(n, mp, reps=8):
                 if prof and prof[0]["name"].startswith("tc_"):
                     ent["tensor_tflops_executed"] = round(3 * 8.0 * (1 << (n + k)) / (ms / 1e3) / 1e12, 1)
                     ent["tensor_frac"] = round(ent["tensor_tflops_executed"] / tf32, 4)
+                elif prof and prof[0]["name"].startswith("tcbf_"):  # six bf16 products
+                    ent["tensor_tflops_executed"] = round(6 * 8.0 * (1 << (n + k)) / (ms / 1e3) / 1e12, 1)
+                    ent["tensor_frac"] = round(ent["tensor_tflops_executed"] / bf16, 4)
                 # error of one more application on 8 sampled slices, against the oracle
                 g0 = gates[0]
                 ts = rng.integers(0, 1 << (n - k), 8)
@@ -437,7 +444,7 @@ def sweep_bench(n, mp, reps=8):
     capi.cast_set_tensor_mode(tc0)
     capi.cast_set_f64_mode(f640)
     return {"n_qubits": n, "gates_per_point": reps, "gates_per_point_c128_k5plus": 2,
-            "tf32_peak": round(tf32, 1), "tf32_peak_source": tsrc, "results": out}
+            "tf32_peak": round(tf32, 1), "bf16_peak": round(bf16, 1), "tf32_peak_source": tsrc, "results": out}
 
 
 def fusion_ablation(n, families=None, dtypes=("c64", "c128")):

@@ -107,15 +107,20 @@ cast_status cast_sv_copy_from_host_async(cast_sv *sv, const void *host);
  * library picks a diagonal, monomial or dense kernel for the matrix. */
 cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix);
 
-/* Arithmetic for dense, unitary complex64 gates with k = 4, 5, 6 on states of
+/* Arithmetic for dense, unitary complex64 gates with k = 4..7 on states of
  * at least k + 7 qubits (process-wide setting):
  *   CAST_TC_TF32X3 (default): tcgen05 tensor cores, each operand split into
  *     two tf32 parts, three products accumulated in fp32, and each slice's
  *     norm restored to its input norm (fp32-class accuracy, unbiased);
+ *   CAST_TC_BF16X6: as CAST_TC_TF32X3, but k = 4, 5 gates split each operand
+ *     into three bf16 parts (the first two truncated, so the remainders are
+ *     exact, the last rounded) and accumulate the six products of weight
+ *     above 2^-24 (kind::f16); k = 6, 7 stay on 3xTF32;
  *   CAST_TC_OFF: fp32 FMA on the CUDA cores for every gate.
  * Other gates are unaffected.  CAST_ERR_ARG for an unknown mode. */
 #define CAST_TC_OFF 0
 #define CAST_TC_TF32X3 1
+#define CAST_TC_BF16X6 2
 cast_status cast_set_tensor_mode(int mode);
 int cast_get_tensor_mode(void);
 

@@ -447,7 +447,7 @@ def cast_adjoint_grad(psi, lam, n, gates, params, terms):
     return energy.value, grad[:npar]
 
 
-CAST_TC_OFF, CAST_TC_TF32X3 = 0, 1
+CAST_TC_OFF, CAST_TC_TF32X3, CAST_TC_BF16X6 = 0, 1, 2
 CAST_F64_EMULATED, CAST_F64_NATIVE = 0, 1
 
 

@@ -455,7 +455,7 @@ bool sparse_preferred(const cast_sv *sv, const PreparedGate &g) {
     // FP32 kernels for k = 5 up to ~80% of the dense operation count (15.6 ms
     // dense vs 12.8-15.9), for k = 6, 7 up to ~40% (74 / 145 ms dense vs
     // 32 / 61 ms), and for k = 4 up to 24 operations per amplitude
-    if (tensor_mode_tf32x3() && g.unitary && g.k >= 4) return false;
+    if (tensor_cores_on() && g.unitary && g.k >= 4) return false;
     if (g.k == 4) return (ops >> g.k) <= 24;
     if (g.k == 5) return 5 * ops <= 4 * dense_opcount(g.k);
     return g.k >= 6 && 5 * ops <= 2 * dense_opcount(g.k);

@@ -60,6 +60,7 @@
 #include <atomic>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -96,6 +97,13 @@ struct TcMat<K, false> {
     __device__ __forceinline__ float2 l(int r, int c) const { return hi[(1 << (2 * K)) + r * (1 << K) + c]; }
 };
 
+// The three bf16 pieces of U (each a float holding a bf16-exact value), by
+// value in the launch parameters (24 KB for k = 5).
+template <int K>
+struct TcMatB {
+    float2 p[3][1 << K][1 << K];
+};
+
 template <int K>
 struct TcShape {
     static constexpr int D = 1 << K;           // slice members
@@ -122,22 +130,47 @@ __device__ __forceinline__ float tf32_round(float x) {
 }
 
 
-template <int K>
+// bf16 pieces of an fp32 value: the top 16 bits (8 significant bits), exact
+// remainders, and the nearest bf16 for the last piece (ties away from zero)
+__device__ __forceinline__ float bf16_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFF0000u); }
+__device__ __forceinline__ float bf16_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x8000u) & 0xFFFF0000u);
+}
+// two bf16-exact floats as one TMEM column (lo half: a, hi half: b)
+__device__ __forceinline__ float bf16x2(float a, float b) {
+    return __uint_as_float(__byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632));
+}
+// 128-byte swizzled K-major image of rows of 64 bf16: row r, element c < 64
+__host__ __device__ __forceinline__ uint32_t sw128_b16(int r, int c) {
+    return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + (((c >> 3) ^ (r & 7)) << 4) + (c & 7) * 2);
+}
+
+// W region of shared memory: 3xTF32 W_hi, W_lo (NK x NK fp32 each); split
+// bf16 three pieces of NK rows x 128 bytes (k <= 5: NK <= 64 bf16 per row)
+template <int K, bool BF>
+__host__ __device__ constexpr int tc_w_bytes() { return BF ? 3 * (2 << K) * 128 : 2 * (2 << K) * (2 << K) * 4; }
+
+template <int K, bool BF>
 __global__ void __launch_bounds__(TcShape<K>::NT, TcShape<K>::CTAS_PER_SM)
 k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-           const __grid_constant__ TcMat<K> U, const __grid_constant__ CubeTables st, uint32_t wait_limit,
-           int skip_mma) {
+           const __grid_constant__ std::conditional_t<BF, TcMatB<K>, TcMat<K>> U,
+           const __grid_constant__ CubeTables st, uint32_t wait_limit, int skip_mma) {
     using S = TcShape<K>;
     constexpr int NK = S::NK, MPT = S::MPT;
     constexpr uint32_t IDESC = tc::idesc_tf32(128, NK);
+    // kind::f16: D fp32, A and B bf16, N = NK, M = 128
+    constexpr uint32_t IDESC_BF = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NK >> 3) << 17) | (uint32_t(128 >> 4) << 24);
     constexpr int G = S::GROUPS;
-    constexpr uint32_t COL_AH = NK, COL_AL = 2 * NK, COL_ACC1 = 3 * NK;  // accumulator 0 at column 0
+    // 3xTF32: accumulator 0 at column 0, A_hi, A_lo, accumulator 1;
+    // bf16: accumulators 0, 1, then the three A pieces of NK / 2 columns
+    constexpr uint32_t COL_AH = NK, COL_AL = 2 * NK, COL_ACC1 = BF ? NK : 3 * NK, COL_AB = 2 * NK;
+    static_assert(!BF || K <= 5, "the bf16 pieces of W fill 128-byte rows for k <= 5");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sWhi = base;
-    uint8_t *sWlo = sWhi + NK * NK * 4;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sWlo + NK * NK * 4);
+    uint8_t *sWhi = base;                      // bf16: piece 0
+    uint8_t *sWlo = sWhi + (BF ? NK * 128 : NK * NK * 4);  // bf16: piece 1 (piece 2 after it)
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + tc_w_bytes<K, BF>());
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     float *xnorm = reinterpret_cast<float *>(tslot + 2);  // [2][GROUPS][128] |x|^2 parts of a row
     float *ynorm = xnorm + 2 * G * 128;                   // [GROUPS][128] |y|^2 parts
@@ -149,13 +182,23 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     // ---- prologue: W_hi / W_lo (SW128 K-major), barrier, TMEM
     for (int idx = tid; idx < NK * NK; idx += S::NT) {
         const int r = idx / NK, c = idx % NK;
-        const float2 h = U.h(r >> 1, c >> 1), l = U.l(r >> 1, c >> 1);
-        float vh, vl;
-        if ((r & 1) == (c & 1)) { vh = h.x; vl = l.x; }   // a on the 2x2 diagonal
-        else if (r & 1) { vh = h.y; vl = l.y; }           // b (row im, col re)
-        else { vh = -h.y; vl = -l.y; }                    // -b (row re, col im)
-        *reinterpret_cast<float *>(sWhi + tc::sw128_offset(r, c, NK)) = vh;
-        *reinterpret_cast<float *>(sWlo + tc::sw128_offset(r, c, NK)) = vl;
+        if constexpr (BF) {
+#pragma unroll
+            for (int pc = 0; pc < 3; pc++) {
+                const float2 h = U.p[pc][r >> 1][c >> 1];
+                const float v = (r & 1) == (c & 1) ? h.x : ((r & 1) ? h.y : -h.y);
+                *reinterpret_cast<uint16_t *>(sWhi + pc * NK * 128 + sw128_b16(r, c)) =
+                    uint16_t(__float_as_uint(v) >> 16);
+            }
+        } else {
+            const float2 h = U.h(r >> 1, c >> 1), l = U.l(r >> 1, c >> 1);
+            float vh, vl;
+            if ((r & 1) == (c & 1)) { vh = h.x; vl = l.x; }   // a on the 2x2 diagonal
+            else if (r & 1) { vh = h.y; vl = l.y; }           // b (row im, col re)
+            else { vh = -h.y; vl = -l.y; }                    // -b (row re, col im)
+            *reinterpret_cast<float *>(sWhi + tc::sw128_offset(r, c, NK)) = vh;
+            *reinterpret_cast<float *>(sWlo + tc::sw128_offset(r, c, NK)) = vl;
+        }
     }
     if (tid == 0) tc::mbar_init(mbar, 1);
     if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
@@ -306,21 +349,40 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
 #pragma unroll
                 for (int m = 0; m < MPT / 2; m++) x[m] = stage[s_row ^ st.s_mem[h * (MPT / 2) + m]];
             }
-            float v[MPT];
+            if constexpr (BF) {
+                // three bf16 pieces per real: truncated, truncated remainder,
+                // rounded last remainder (each subtraction exact in fp32); one
+                // column per member holds its (re, im) pair of a piece
+                float p0[MPT / 2], p1[MPT / 2], p2[MPT / 2];
 #pragma unroll
-            for (int m = 0; m < MPT / 2; m++) {
-                v[2 * m] = tf32_trunc(x[m].x);
-                v[2 * m + 1] = tf32_trunc(x[m].y);
-            }
-            tc::tmem_st<MPT>(lane_addr + COL_AH + 2 * j0 + MPT * h, v);
-            // the remainder is rounded to tf32 as well: the tensor cores would
-            // otherwise truncate it, a bias that shrinks the norm gate after gate
+                for (int m = 0; m < MPT / 2; m++) {
+                    const float a0 = bf16_trunc(x[m].x), b0 = bf16_trunc(x[m].y);
+                    const float ar = x[m].x - a0, br = x[m].y - b0;
+                    const float a1 = bf16_trunc(ar), b1 = bf16_trunc(br);
+                    p0[m] = bf16x2(a0, b0);
+                    p1[m] = bf16x2(a1, b1);
+                    p2[m] = bf16x2(bf16_round(ar - a1), bf16_round(br - b1));
+                }
+                tc::tmem_st<MPT / 2>(lane_addr + COL_AB + j0 + (MPT / 2) * h, p0);
+                tc::tmem_st<MPT / 2>(lane_addr + COL_AB + NK / 2 + j0 + (MPT / 2) * h, p1);
+                tc::tmem_st<MPT / 2>(lane_addr + COL_AB + NK + j0 + (MPT / 2) * h, p2);
+            } else {
+                float v[MPT];
 #pragma unroll
-            for (int m = 0; m < MPT / 2; m++) {
-                v[2 * m] = tf32_round(x[m].x - v[2 * m]);
-                v[2 * m + 1] = tf32_round(x[m].y - v[2 * m + 1]);
+                for (int m = 0; m < MPT / 2; m++) {
+                    v[2 * m] = tf32_trunc(x[m].x);
+                    v[2 * m + 1] = tf32_trunc(x[m].y);
+                }
+                tc::tmem_st<MPT>(lane_addr + COL_AH + 2 * j0 + MPT * h, v);
+                // the remainder is rounded to tf32 as well: the tensor cores would
+                // otherwise truncate it, a bias that shrinks the norm gate after gate
+#pragma unroll
+                for (int m = 0; m < MPT / 2; m++) {
+                    v[2 * m] = tf32_round(x[m].x - v[2 * m]);
+                    v[2 * m + 1] = tf32_round(x[m].y - v[2 * m + 1]);
+                }
+                tc::tmem_st<MPT>(lane_addr + COL_AL + 2 * j0 + MPT * h, v);
             }
-            tc::tmem_st<MPT>(lane_addr + COL_AL + 2 * j0 + MPT * h, v);
 #pragma unroll
             for (int m = 0; m < MPT / 2; m++) {
                 xs = fmaf(x[m].x, x[m].x, xs);
@@ -340,18 +402,37 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         if (__syncthreads_or(failed)) break;
         tc::fence_after_sync();
         if (tid == 0 && !skip_mma) {
-            const uint32_t wH = tc::smem_u32(sWhi), wL = tc::smem_u32(sWlo);
+            const uint32_t wH = tc::smem_u32(sWhi);
             const uint32_t dacc = taddr + (buf ? COL_ACC1 : 0u);
             uint32_t acc = 0;
+            if constexpr (BF) {
+                // six products (piece of x, piece of W), smallest weight first
+                constexpr int PA[6] = {2, 1, 0, 1, 0, 0}, PW[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
-            for (int pr = 0; pr < 3; pr++) {
-                const uint32_t acol = pr == 0 ? COL_AL : COL_AH;  // lo*W_hi, hi*W_lo, hi*W_hi
-                const uint32_t w = pr == 1 ? wL : wH;
+                for (int pr = 0; pr < 6; pr++) {
 #pragma unroll
-                for (int s = 0; s < NK / 8; s++) {
-                    const uint32_t kw = uint32_t((s >> 2) * (NK / 8) * 1024 + (s & 3) * 32);
-                    tc::mma_tf32_ts(dacc, taddr + acol + 8 * s, tc::smem_desc_sw128(w + kw), IDESC, acc);
-                    acc = 1;
+                    for (int s = 0; s < NK / 16; s++) {
+                        const uint32_t a = taddr + COL_AB + uint32_t(PA[pr] * (NK / 2) + 8 * s);
+                        const uint64_t b = tc::smem_desc_sw128(wH + uint32_t(PW[pr] * NK * 128 + 32 * s));
+                        asm volatile(
+                            "{\n\t.reg .pred pp;\n\tsetp.ne.b32 pp, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, pp;\n\t}" ::"r"(dacc),
+                            "r"(a), "l"(b), "r"(IDESC_BF), "r"(acc));
+                        acc = 1;
+                    }
+                }
+            } else {
+                const uint32_t wL = tc::smem_u32(sWlo);
+#pragma unroll
+                for (int pr = 0; pr < 3; pr++) {
+                    const uint32_t acol = pr == 0 ? COL_AL : COL_AH;  // lo*W_hi, hi*W_lo, hi*W_hi
+                    const uint32_t w = pr == 1 ? wL : wH;
+#pragma unroll
+                    for (int s = 0; s < NK / 8; s++) {
+                        const uint32_t kw = uint32_t((s >> 2) * (NK / 8) * 1024 + (s & 3) * 32);
+                        tc::mma_tf32_ts(dacc, taddr + acol + 8 * s, tc::smem_desc_sw128(w + kw), IDESC, acc);
+                        acc = 1;
+                    }
                 }
             }
             tc::mma_commit(mbar);
@@ -398,51 +479,90 @@ float host_tf32(float x) {
     return r;
 }
 
-template <int K>
+template <int K, bool BF>
 size_t tc_smem_bytes() {
     using S = TcShape<K>;
-    const size_t need = 1024 + size_t(S::NK) * S::NK * 4 * 2 + 64 + 3 * 4 * 128 * S::GROUPS + 16 +
+    const size_t need = 1024 + size_t(tc_w_bytes<K, BF>()) + 64 + 3 * 4 * 128 * S::GROUPS + 16 +
                         size_t(S::NT / 32) * 4096 * S::STAGES;
     // at most CTAS_PER_SM resident CTAs per SM (228 KB of shared memory each)
     const size_t floor = (228 * 1024) / (S::CTAS_PER_SM + 1) + 1024;
     return need > floor ? need : floor;
 }
 
-template <int K>
+// bf16 pieces of a double, on the host: the top 8 significant bits
+// (truncated) of the float nearest w, and the nearest bf16 of w
+float host_bf16_trunc(double w) {
+    const float f = (float)w;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u &= 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+float host_bf16_round(double w) {
+    const float f = (float)w;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x8000u) & 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+template <int K, bool BF>
 cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
     constexpr int D = 1 << K;
     using S = TcShape<K>;
-    std::vector<float2> hl(size_t(2) << (2 * K));
-    for (int r = 0; r < D; r++)
-        for (int c = 0; c < D; c++) {
-            const cplx u = g.m[size_t(r) * D + c];
-            const float hr = host_tf32((float)u.real()), hi = host_tf32((float)u.imag());
-            hl[size_t(r) * D + c] = make_float2(hr, hi);
-            hl[(size_t(1) << (2 * K)) + size_t(r) * D + c] =
-                make_float2(host_tf32((float)(u.real() - (double)hr)), host_tf32((float)(u.imag() - (double)hi)));
-        }
-    TcMat<K> U;
-    if constexpr (K <= 5) {
-        std::memcpy(U.hi, hl.data(), sizeof(U.hi));
-        std::memcpy(U.lo, hl.data() + (size_t(1) << (2 * K)), sizeof(U.lo));
+    std::conditional_t<BF, TcMatB<K>, TcMat<K>> U;
+    if constexpr (BF) {
+        // w = p0 + p1 + p2: p0, p1 truncated (the remainders are exact in
+        // double), p2 the nearest bf16 of what is left
+        for (int r = 0; r < D; r++)
+            for (int c = 0; c < D; c++) {
+                const cplx u = g.m[size_t(r) * D + c];
+                float pr[3], pi[3];
+                double wr = u.real(), wi = u.imag();
+                pr[0] = host_bf16_trunc(wr), pi[0] = host_bf16_trunc(wi);
+                wr -= pr[0], wi -= pi[0];
+                pr[1] = host_bf16_trunc(wr), pi[1] = host_bf16_trunc(wi);
+                wr -= pr[1], wi -= pi[1];
+                pr[2] = host_bf16_round(wr), pi[2] = host_bf16_round(wi);
+                for (int pc = 0; pc < 3; pc++) U.p[pc][r][c] = make_float2(pr[pc], pi[pc]);
+            }
     } else {
-        const void *dev = nullptr;
-        cast_status st = upload_matrix(sv, hl.data(), hl.size() * sizeof(float2), &dev);
-        if (st != CAST_OK) return st;
-        U.hi = static_cast<const float2 *>(dev);
+        std::vector<float2> hl(size_t(2) << (2 * K));
+        for (int r = 0; r < D; r++)
+            for (int c = 0; c < D; c++) {
+                const cplx u = g.m[size_t(r) * D + c];
+                const float hr = host_tf32((float)u.real()), hi = host_tf32((float)u.imag());
+                hl[size_t(r) * D + c] = make_float2(hr, hi);
+                hl[(size_t(1) << (2 * K)) + size_t(r) * D + c] =
+                    make_float2(host_tf32((float)(u.real() - (double)hr)), host_tf32((float)(u.imag() - (double)hi)));
+            }
+        if constexpr (K <= 5) {
+            std::memcpy(U.hi, hl.data(), sizeof(U.hi));
+            std::memcpy(U.lo, hl.data() + (size_t(1) << (2 * K)), sizeof(U.lo));
+        } else {
+            const void *dev = nullptr;
+            cast_status st = upload_matrix(sv, hl.data(), hl.size() * sizeof(float2), &dev);
+            if (st != CAST_OK) return st;
+            U.hi = static_cast<const float2 *>(dev);
+        }
     }
     Targets tg;
     for (int i = 0; i < CAST_MAX_K; i++) tg.q[i] = i < K ? g.q[i] : 0;
     const uint64_t ntiles = uint64_t(1) << (sv->n - K - 7);
-    const size_t smem = tc_smem_bytes<K>();
-    CAST_CUDA(cudaFuncSetAttribute(k_dense_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = tc_smem_bytes<K, BF>();
+    CAST_CUDA(cudaFuncSetAttribute(k_dense_tc<K, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t cap = uint64_t(sm_count_cached()) * S::CTAS_PER_SM;
     const uint64_t grid = ntiles < cap ? ntiles : cap;
-    ProfScope ps(sv->stream, "tc_k" + std::to_string(K) + "_c64", 16.0 * double(uint64_t(1) << sv->n),
+    ProfScope ps(sv->stream, std::string(BF ? "tcbf_k" : "tc_k") + std::to_string(K) + "_c64",
+                 16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
     const uint32_t inject = take_inject_limit();
     const CubeTables st = make_cube_tables(g.q, K);
-    k_dense_tc<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
+    k_dense_tc<K, BF><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
                                                                inject ? inject : kWaitLimit, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
@@ -450,19 +570,21 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
 
 }  // namespace
 
-bool tensor_mode_tf32x3() { return g_tensor_mode.load() == CAST_TC_TF32X3; }
+bool tensor_cores_on() { return g_tensor_mode.load() != CAST_TC_OFF; }
 
 uint32_t take_inject_limit() { return g_inject_limit.exchange(0); }
 
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g) {
-    return g_tensor_mode.load() == CAST_TC_TF32X3 && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary &&
-           g.k >= 4 && g.k <= 6 && sv->n >= g.k + 7;
+    const int mode = g_tensor_mode.load();
+    return mode != CAST_TC_OFF && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary && g.k >= 4 &&
+           g.k <= (mode == CAST_TC_BF16X6 ? 5 : 6) && sv->n >= g.k + 7;
 }
 
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g) {
-    if (g.k == 4) return run_tc<4>(sv, g);
-    if (g.k == 5) return run_tc<5>(sv, g);
-    if (g.k == 6) return run_tc<6>(sv, g);
+    const bool bf = g_tensor_mode.load() == CAST_TC_BF16X6;
+    if (g.k == 4) return bf ? run_tc<4, true>(sv, g) : run_tc<4, false>(sv, g);
+    if (g.k == 5) return bf ? run_tc<5, true>(sv, g) : run_tc<5, false>(sv, g);
+    if (g.k == 6) return run_tc<6, false>(sv, g);
     return fail(CAST_ERR_UNSUPPORTED, "tensor-core path covers k = 4, 5, 6");
 }
 
@@ -484,7 +606,8 @@ cast_status take_device_error() {
 extern "C" {
 
 cast_status cast_set_tensor_mode(int mode) {
-    if (mode != CAST_TC_OFF && mode != CAST_TC_TF32X3) return cast::fail(CAST_ERR_ARG, "unknown tensor mode");
+    if (mode != CAST_TC_OFF && mode != CAST_TC_TF32X3 && mode != CAST_TC_BF16X6)
+        return cast::fail(CAST_ERR_ARG, "unknown tensor mode");
     cast::g_tensor_mode = mode;
     return CAST_OK;
 }

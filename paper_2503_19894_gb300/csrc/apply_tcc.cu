@@ -477,7 +477,7 @@ int tcc_error_flag_take() {
 }
 
 bool tcc_eligible(const cast_sv *sv, const PreparedGate &g) {
-    return tensor_mode_tf32x3() && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary &&
+    return tensor_cores_on() && sv->dt == CAST_C64 && g.cls == CLS_DENSE && g.unitary &&
            (g.k == 7 || (g.k == 6 && kTcc6)) && sv->n >= g.k + 7;
 }
 

@@ -173,7 +173,7 @@ cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
 bool tcc_eligible(const cast_sv *sv, const PreparedGate &g);  // dense k = 6, 7, K-chunked (apply_tcc.cu)
 cast_status launch_gate_tcc(cast_sv *sv, const PreparedGate &g);
 int tcc_error_flag_take();          // the chunked kernel's bounded-wait error flag, cleared
-bool tensor_mode_tf32x3();          // cast_set_tensor_mode(CAST_TC_TF32X3) in effect
+bool tensor_cores_on();             // cast_set_tensor_mode other than CAST_TC_OFF in effect
 uint32_t take_inject_limit();       // cast_debug_inject_timeout's pending limit, cleared (0: none)
 // Autotuned launch width (blocks per SM) of a CUDA-core kernel, or def.
 int tuned_blocks_per_sm(cast_dtype dt, int k, int cls, int def);

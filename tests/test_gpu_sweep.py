@@ -18,7 +18,7 @@ from paper_2503_19894_gb300 import capi
 pytestmark = pytest.mark.gpu
 
 TOL = {"c64": 1e-5, "c128": 1e-12}
-MODES = [("c64", "fp32"), ("c64", "tf32x3"), ("c128", "double-float"), ("c128", "fp64")]
+MODES = [("c64", "fp32"), ("c64", "tf32x3"), ("c64", "bf16x6"), ("c128", "double-float"), ("c128", "fp64")]
 
 
 @pytest.fixture
@@ -30,7 +30,7 @@ def modes():
 
 
 def set_mode(mode):
-    capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3 if mode == "tf32x3" else capi.CAST_TC_OFF)
+    capi.cast_set_tensor_mode({"tf32x3": capi.CAST_TC_TF32X3, "bf16x6": capi.CAST_TC_BF16X6}.get(mode, capi.CAST_TC_OFF))
     capi.cast_set_f64_mode(capi.CAST_F64_NATIVE if mode == "fp64" else capi.CAST_F64_EMULATED)
 
 
