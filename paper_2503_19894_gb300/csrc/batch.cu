@@ -58,6 +58,7 @@ struct BEntry {
     int32_t mat;     // matrix slot (16 complex entries)
     int32_t kind;    // BK_FIXED or the rotation's generator
     int32_t param;   // parameter index (global), -1 if fixed
+    int32_t skip;    // bit j: member j has an identity row and column (not loaded or stored)
 };
 
 struct BTerm {
@@ -291,12 +292,14 @@ k_batch_gate(typename A::Amp *__restrict__ psi, const BEntry *__restrict__ entri
         typename A::V v[4];
         const int d = 1 << e.k;
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (j < d) v[j] = A::in(psi[a[j]]);
+        for (int j = 0; j < 4; j++) {
+            v[j] = A::zero();
+            if (j < d && !((e.skip >> j) & 1)) v[j] = A::in(psi[a[j]]);
+        }
         apply_small<A>(mats + size_t(e.mat) * 16, e.k, false, v);
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            if (j < d) psi[a[j]] = A::out(v[j]);
+            if (j < d && !((e.skip >> j) & 1)) psi[a[j]] = A::out(v[j]);
     }
 }
 
@@ -399,11 +402,13 @@ k_batch_back(typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ la
         typename A::V v[4], l[4];
         const int d = 1 << e.k;
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (j < d) {
+        for (int j = 0; j < 4; j++) {
+            v[j] = l[j] = A::zero();
+            if (j < d && !((e.skip >> j) & 1)) {
                 v[j] = A::in(psi[a[j]]);
                 l[j] = A::in(lam[a[j]]);
             }
+        }
         if (e.kind != BK_FIXED) {  // 1-qubit rotation: Im<lam|P|psi> on the slice
             gparam = e.param;
             if (e.kind == BK_RX) {         // Im(conj(l0) v1 + conj(l1) v0)
@@ -421,7 +426,7 @@ k_batch_back(typename A::Amp *__restrict__ psi, typename A::Amp *__restrict__ la
         apply_small<A>(mats + size_t(e.mat) * 16, e.k, true, l);
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            if (j < d) {
+            if (j < d && !((e.skip >> j) & 1)) {
                 psi[a[j]] = A::out(v[j]);
                 lam[a[j]] = A::out(l[j]);
             }
@@ -689,6 +694,16 @@ cast_status cast_batch_create(int n_instances, const cast_circuit *circuits, con
                     return st;
                 }
                 for (size_t j = 0; j < m.size(); j++) slot[j] = make_double2(m[j].real(), m[j].imag());
+                // members whose row and column are those of the identity stay
+                // in memory untouched (CZ: three of four; a rotation never)
+                const int d = 1 << g.k;
+                for (int j = 0; j < d; j++) {
+                    bool id = m[size_t(j) * d + j] == cplx(1.0, 0.0);
+                    for (int o = 0; o < d && id; o++)
+                        if (o != j && (m[size_t(j) * d + o] != cplx(0.0, 0.0) || m[size_t(o) * d + j] != cplx(0.0, 0.0)))
+                            id = false;
+                    if (id) e.skip |= 1 << j;
+                }
             }
             b->fixed_mats.insert(b->fixed_mats.end(), slot.begin(), slot.end());
             b->entries.push_back(e);
