@@ -104,11 +104,21 @@ struct TcMatB {
     float2 p[3][1 << K][1 << K];
 };
 
+// k = 4 with two warps per TMEM lane quarter (eight members each, eight
+// warps per CTA, four CTAs per SM, 56 registers) instead of one (sixteen
+// members, four warps): twice the warps and loads in flight per SM, measured
+// no faster (2.88-2.93 against 2.88-2.90 ms per 30-qubit gate with 3xTF32;
+// 3.08-3.14 against 2.85-2.88 ms with split bf16), so it stays off
+constexpr bool kTc4Split = false;
+
 template <int K>
 struct TcShape {
     static constexpr int D = 1 << K;           // slice members
     static constexpr int NK = 2 * D;           // GEMM N = K (reals)
-    static constexpr int MPT = D < 16 ? D : 16;  // members per thread
+    static constexpr int MPT = (K == 4 && kTc4Split) ? 8 : (D < 16 ? D : 16);  // members per thread
+    static constexpr int MB = MPT == 8 ? 3 : 4;  // member bits of a warp's cube
+    static constexpr int CUBE = 32 * MPT;      // amplitudes of a warp's cube
+    static constexpr int ROUNDS = CUBE / 64;   // 16-byte chunks per lane
     static constexpr int GROUPS = D / MPT;     // warps per TMEM lane quarter
     static constexpr int NT = 128 * GROUPS;    // threads per CTA
     static constexpr int NCOL = 4 * NK;        // two accumulators, A_hi, A_lo
@@ -211,11 +221,11 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
 
     // this warp's staging cubes (STAGES x 512 amplitudes), after the norm arrays
     constexpr int NS = S::STAGES;
-    float2 *stages = reinterpret_cast<float2 *>(ynorm + G * 128 + 4) + warp * (512 * NS);
+    float2 *stages = reinterpret_cast<float2 *>(ynorm + G * 128 + 4) + warp * (S::CUBE * NS);
     // member offset of this warp group's first member j0 (targets q4, q5 only)
     uint64_t off0 = 0;
 #pragma unroll
-    for (int i = 4; i < K; i++)
+    for (int i = S::MB; i < K; i++)
         if ((j0 >> i) & 1) off0 += uint64_t(1) << tg.q[i];
     const uint64_t g_lane = st.g_lane[lane];
     const uint32_t s_lane = st.s_lane[lane], s_row = st.s_row[lane];
@@ -225,20 +235,20 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         const float2 *b = sv + cube_base(t);
         const uint32_t d = tc::smem_u32(stage);
 #pragma unroll
-        for (int j = 0; j < 8; j++)
+        for (int j = 0; j < S::ROUNDS; j++)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ st.s_j[j]) >> 1) * 16u),
                          "l"(b + st.g_j[j])
                          : "memory");
     };
-    auto load_regs = [&](uint64_t t, float4 (&c)[8]) {
+    auto load_regs = [&](uint64_t t, float4 (&c)[S::ROUNDS]) {
         const float2 *b = sv + cube_base(t);
 #pragma unroll
-        for (int j = 0; j < 8; j++) c[j] = __ldcs(reinterpret_cast<const float4 *>(b + st.g_j[j]));
+        for (int j = 0; j < S::ROUNDS; j++) c[j] = __ldcs(reinterpret_cast<const float4 *>(b + st.g_j[j]));
     };
-    auto regs_to_stage = [&](const float4 (&c)[8], float2 *stage) {
+    auto regs_to_stage = [&](const float4 (&c)[S::ROUNDS], float2 *stage) {
         float4 *s4 = reinterpret_cast<float4 *>(stage);
 #pragma unroll
-        for (int j = 0; j < 8; j++) s4[(s_lane ^ st.s_j[j]) >> 1] = c[j];
+        for (int j = 0; j < S::ROUNDS; j++) s4[(s_lane ^ st.s_j[j]) >> 1] = c[j];
     };
 
     // drain one tile's accumulator: restore each slice's norm, store to HBM
@@ -301,12 +311,12 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
         float2 *b = sv + cube_base(t);
         const float4 *s4 = reinterpret_cast<const float4 *>(stage);
 #pragma unroll
-        for (int j = 0; j < 8; j++)
+        for (int j = 0; j < S::ROUNDS; j++)
             __stcs(reinterpret_cast<float4 *>(b + st.g_j[j]), s4[(s_lane ^ st.s_j[j]) >> 1]);
         __syncwarp();
     };
 
-    float4 nxt[8];  // register prefetch (one stage only)
+    float4 nxt[S::ROUNDS];  // register prefetch (one stage only)
     const uint64_t step = gridDim.x;
     uint64_t tile = blockIdx.x, prev = ~uint64_t(0);
     uint32_t phase = 0;
@@ -316,7 +326,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     if constexpr (NS > 1) {
 #pragma unroll
         for (int si = 0; si < NS; si++) {
-            if (tile + si * step < ntiles) copy_async(tile + si * step, stages + si * 512);
+            if (tile + si * step < ntiles) copy_async(tile + si * step, stages + si * S::CUBE);
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
     } else {
@@ -324,7 +334,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     }
     int si = 0;  // stage of the current tile
     while (tile < ntiles) {
-        float2 *stage = stages + si * 512;
+        float2 *stage = stages + si * S::CUBE;
         // ---- this thread's slice row from the staged cube
         if constexpr (NS > 1) {
             asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
@@ -458,7 +468,7 @@ k_dense_tc(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Tar
     if constexpr (NS > 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
     failed = __syncthreads_or(failed);
     if (failed) phase ^= 1u;  // the wait that ran out is retried below
-    if (!failed && prev != ~uint64_t(0)) epilogue(prev, buf ? 0u : COL_ACC1, buf ^ 1, x_prev, stages + si * 512);
+    if (!failed && prev != ~uint64_t(0)) epilogue(prev, buf ? 0u : COL_ACC1, buf ^ 1, x_prev, stages + si * S::CUBE);
     if (failed) {
         if (tid == 0) atomicOr(&g_tc_error, 1);
         tc::mbar_wait(mbar, phase, wait_limit);  // let an MMA in flight finish before freeing TMEM
@@ -483,7 +493,7 @@ template <int K, bool BF>
 size_t tc_smem_bytes() {
     using S = TcShape<K>;
     const size_t need = 1024 + size_t(tc_w_bytes<K, BF>()) + 64 + 3 * 4 * 128 * S::GROUPS + 16 +
-                        size_t(S::NT / 32) * 4096 * S::STAGES;
+                        size_t(S::NT / 32) * S::CUBE * 8 * S::STAGES;
     // at most CTAS_PER_SM resident CTAs per SM (228 KB of shared memory each)
     const size_t floor = (228 * 1024) / (S::CTAS_PER_SM + 1) + 1024;
     return need > floor ? need : floor;
@@ -561,7 +571,7 @@ cast_status run_tc(cast_sv *sv, const PreparedGate &g) {
                  16.0 * double(uint64_t(1) << sv->n),
                  8.0 * double(uint64_t(1) << (sv->n + K)));
     const uint32_t inject = take_inject_limit();
-    const CubeTables st = make_cube_tables(g.q, K);
+    const CubeTables st = make_cube_tables(g.q, K, S::MB);
     k_dense_tc<K, BF><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<float2 *>(sv->data), ntiles, tg, U, st,
                                                                inject ? inject : kWaitLimit, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());

@@ -14,8 +14,9 @@ namespace cast {
 // each of r0..r3 at a position >= 4 to a free slot bit among 1..3, so that
 // the 16 rows of a half-warp land in different 8-byte bank pairs (when
 // qubit 0 is a target only three slot bits are free: 2-way at most).
-CubeTables make_cube_tables(const int *q, int k) {
-    const int mb = k < 4 ? k : 4;
+CubeTables make_cube_tables(const int *q, int k) { return make_cube_tables(q, k, k < 4 ? k : 4); }
+
+CubeTables make_cube_tables(const int *q, int k, int mb) {
     const int nbits = 5 + mb;
     int rpos[5], mpos[4] = {0, 0, 0, 0}, abit[9];
     int nr = 0, nm = 0, nb = 0;

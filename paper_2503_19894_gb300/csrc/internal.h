@@ -165,6 +165,8 @@ struct CubeTables {
                           // so rows move as 16-byte pairs (conflict-free, half the accesses)
 };
 CubeTables make_cube_tables(const int *q, int k);
+// the same with the cube's member bits given: the first mb targets (mb <= min(k, 4))
+CubeTables make_cube_tables(const int *q, int k, int mb);
 
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
