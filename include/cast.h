@@ -278,7 +278,9 @@ typedef struct {
 } cast_options;
 
 /* Measure the cost table on a scratch state of n_qubits (allocated and
- * freed here) on cuda_stream: one gate of every size 1..CAST_MAX_K and class
+ * freed here, filled with seeded pseudo-random amplitudes so that kernels
+ * which skip work on zero values are timed as on a state in use) on
+ * cuda_stream: one gate of every size 1..CAST_MAX_K and class
  * (diagonal, monomial, dense), for the CUDA-core kernels at launch widths of
  * 1, 2, 4 and 8 blocks per SM keeping the fastest; then, for k = 3..7 and
  * n_qubits >= 12, the sparse kernel on a matrix with two entries per row
