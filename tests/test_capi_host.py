@@ -175,3 +175,30 @@ def test_fuse_reports_required_capacity():
     n = ctypes.c_int(1)
     st = lib.cast_fuse(ctypes.byref(circ.c), None, ctypes.byref(o), ctypes.byref(n), None, None, None, None)
     assert st == 1 and n.value == len(gates)
+
+
+def test_plan_default_cost_constant_follows_the_state_type():
+    """cast_plan_create (host only) with amp_ops_per_pass = 0 takes the state
+    type's constant: 82 for complex64, 64 for complex128 in the emulated mode,
+    2 with native FP64; the plans equal those made with the constant given."""
+    import workloads as W
+    n = 14
+    gates = W.benchmark_family("HES", n, seed=1)[:300]
+    old = capi.cast_get_f64_mode()
+
+    def info(dtype, P):
+        p = capi.cast_plan_create(n, gates, opts=capi.options("adaptive", 5, amp_ops_per_pass=P), dtype=dtype)
+        out = capi.cast_plan_info(p)
+        capi.cast_plan_destroy(p)
+        return out
+
+    try:
+        capi.cast_set_f64_mode(capi.CAST_F64_EMULATED)
+        assert info("c64", 0) == info("c64", 82)
+        assert info("c128", 0) == info("c128", 64)
+        capi.cast_set_f64_mode(capi.CAST_F64_NATIVE)
+        assert info("c128", 0) == info("c128", 2)
+        # the constants differ in effect on this circuit: 2 fuses less than 64
+        assert info("c128", 2)[0] > info("c128", 64)[0]
+    finally:
+        capi.cast_set_f64_mode(old)
