@@ -49,22 +49,28 @@ namespace {
 
 __device__ int g_tcc_error;
 
+// k = 6 streams W (64 KB of buffers) instead of keeping it resident (128 KB),
+// for four cube stages per worker warp instead of two: measured 4.26-4.31
+// against 3.58-3.62 ms per 30-qubit gate (W re-read from L2 every tile), so off
+constexpr bool kTcc6Stream = false;
+
 template <int K>
 struct TccShape {
     static constexpr int D = 1 << K;            // slice members
     static constexpr int N = 2 * D;             // output reals = accumulator columns (MMA N)
     static constexpr int CHUNKS = D / 16;       // K chunks of 16 members (32 reals)
-    // k = 6: W (128 KB) stays resident and two accumulators alternate between
-    // tiles, so a tile's epilogue overlaps the next tile's MMAs; k = 7: W is
+    // k = 6: two accumulators alternate between tiles, so a tile's epilogue
+    // overlaps the next tile's MMAs; W (128 KB) resident, or streamed (kTcc6Stream)
+    // to make room for four cube stages per warp instead of two.  k = 7: W is
     // streamed one chunk ahead and the one 256-column accumulator is all TMEM allows
-    static constexpr bool RESIDENT_W = K == 6;
+    static constexpr bool RESIDENT_W = K == 6 && !kTcc6Stream;
     static constexpr int NACC = K == 6 ? 2 : 1;
     static constexpr int COL_A = NACC * N;      // TMEM: accumulators, then 2 A buffers of 64 columns
     static constexpr uint32_t CHUNK_BYTES = uint32_t(N) * 128u;  // W^T chunk, hi or lo
-    static constexpr uint32_t W_BYTES = 4u * 32768u;             // W region of shared memory
+    static constexpr uint32_t W_BYTES = RESIDENT_W ? 2u * CHUNKS * CHUNK_BYTES : 4u * CHUNK_BYTES;  // W region
+    static constexpr int NS = (K == 6 && !RESIDENT_W) ? 4 : 2;  // cube stages per worker warp
     static constexpr int COLS = 512;
     static_assert(COL_A + 128 <= COLS, "TMEM columns");
-    static_assert(RESIDENT_W ? 2 * CHUNKS * CHUNK_BYTES == W_BYTES : 4 * CHUNK_BYTES == W_BYTES, "W bytes");
 };
 constexpr uint32_t kTccWaitLimit = 1u << 26;
 // dense 6-qubit gates take this kernel rather than apply_tc.cu's resident-W one
@@ -124,8 +130,8 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
     }
     // W: k = 7 [2 buffers][hi, lo] x CB; k = 6 [hi chunks 0..3][lo chunks 0..3] x CB
     uint8_t *sB = ws_smem;
-    float2 *cubes = reinterpret_cast<float2 *>(ws_smem + S::W_BYTES);   // [8 warps][2 stages][512]
-    float2 *outc = cubes + kWsWorkers * 2 * 512;                         // [8 warps][512]
+    float2 *cubes = reinterpret_cast<float2 *>(ws_smem + S::W_BYTES);   // [8 warps][NS stages][512]
+    float2 *outc = cubes + kWsWorkers * S::NS * 512;                     // [8 warps][512]
     float *xnorm = reinterpret_cast<float *>(outc + kWsWorkers * 512);  // [2 groups][128]
     float *ynorm = xnorm + 256;                                          // [2 groups][128]
     uint64_t *bar_a = reinterpret_cast<uint64_t *>(ynorm + 256);
@@ -256,11 +262,11 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
         auto cube_base = [&](uint64_t tile, int c) {
             return slice_base<K>(tile * 128 + uint64_t(32 * quarter), tg) + group_off(c) + g_lane;
         };
-        float2 *my_cubes = cubes + warp * (2 * 512);
+        float2 *my_cubes = cubes + warp * (S::NS * 512);
         float2 *my_out = outc + warp * 512;
-        auto copy_async = [&](uint64_t j) {  // job j into stage (j / 2) & 1 of this warp's ring
+        auto copy_async = [&](uint64_t j) {  // job j into stage (j / 2) % NS of this warp's ring
             const float2 *b = sv + cube_base(job_tile(j), int(j % CHUNKS));
-            const uint32_t d = tc::smem_u32(my_cubes + ((j >> 1) & 1) * 512);
+            const uint32_t d = tc::smem_u32(my_cubes + ((j >> 1) % S::NS) * 512);
 #pragma unroll
             for (int jj = 0; jj < 8; jj++)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + ((s_lane ^ st.s_j[jj]) >> 1) * 16u),
@@ -323,7 +329,7 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
             mbar_arrive(&bar_e[a]);
             return true;
         };
-        for (int p = 0; p < 2; p++) {
+        for (int p = 0; p < S::NS; p++) {
             const uint64_t jp = uint64_t(g) + 2 * uint64_t(p);
             if (jp < njobs) copy_async(jp);
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -339,9 +345,9 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
                 break;
             }
             tc::fence_after_sync();
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(S::NS - 1) : "memory");
             __syncwarp();
-            const float2 *stage = my_cubes + ((j >> 1) & 1) * 512;
+            const float2 *stage = my_cubes + ((j >> 1) % S::NS) * 512;
             float xa = 0.f, xb = 0.f;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -379,9 +385,9 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
             tc::tmem_wait_st();
             tc::fence_before_sync();
             mbar_arrive(&bar_a[g]);
-            // the stage of job j is in TMEM now: refill it with this warp's job j + 4
+            // the stage of job j is in TMEM now: refill it with this warp's job j + 2 NS
             __syncwarp();
-            if (j + 4 < njobs) copy_async(j + 4);
+            if (j + 2 * S::NS < njobs) copy_async(j + 2 * S::NS);
             asm volatile("cp.async.commit_group;" ::: "memory");
             if (c == g && t >= 1) {  // first chunk of tile t queued: drain tile t - 1
                 const float xt = xs;
@@ -405,7 +411,11 @@ k_dense_tcc_ws(float2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__
 }
 
 // W, staging and output cubes, norms, 14 barriers, TMEM slot and fail flag
-size_t tcc_ws_smem_bytes() { return 131072 + size_t(kWsWorkers) * 3 * 512 * 8 + 2 * 256 * 4 + 14 * 8 + 8; }
+template <int K>
+size_t tcc_ws_smem_bytes() {
+    using S = TccShape<K>;
+    return S::W_BYTES + size_t(kWsWorkers) * (S::NS + 1) * 512 * 8 + 2 * 256 * 4 + 14 * 8 + 8;
+}
 
 // host-side tf32 rounding (nearest, ties away from zero, as cvt.rna)
 float host_tf32_rna(float x) {
@@ -455,8 +465,7 @@ cast_status run_tcc(cast_sv *sv, const PreparedGate &g) {
                  8.0 * double(uint64_t(1) << (sv->n + K)));
     const uint32_t inject = take_inject_limit();
     static_assert(K == 6 || K == 7, "the chunked kernel is built for k = 6, 7");
-    static_assert(S::W_BYTES == 131072, "W region");
-    const size_t smem = tcc_ws_smem_bytes();
+    const size_t smem = tcc_ws_smem_bytes<K>();
     CAST_CUDA(cudaFuncSetAttribute(k_dense_tcc_ws<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_dense_tcc_ws<K><<<(unsigned)grid, kWsThreads, smem, sv->stream>>>(
         reinterpret_cast<float2 *>(sv->data), ntiles, tg, W, ct, inject ? inject : kTccWaitLimit, inject ? 1 : 0);
