@@ -179,6 +179,17 @@ int cast_get_sparse_mode(void);
 #define CAST_PEAK_BF16 1
 cast_status cast_measure_tensor_peak(int kind, double *tflops);
 
+/* Issue cost of one small tensor-core MMA on the current GPU, in SM clock
+ * cycles: one CTA per SM issues 8192 back-to-back tcgen05.mma kind::f16
+ * instructions (M = 128, K = 16, N = n_cols, bf16 zero operands, A from tensor
+ * memory if a_in_tmem else from shared memory, one fp32 accumulator) and the
+ * SM's clock64 is read from the first issue to the completion of their
+ * commit; *cycles_per_mma is the mean over SMs, best of two timed launches.
+ * It is the measurement behind the complex128 digit kernels' operand layout
+ * (one MMA over stacked digit blocks instead of many narrow ones).
+ * CAST_ERR_ARG unless n_cols is 16..256 and a multiple of 16. */
+cast_status cast_measure_mma_issue(int n_cols, int a_in_tmem, double *cycles_per_mma);
+
 /* Failure-detection test hook.  The next tensor-core gate launch waits on an
  * MMA completion that never comes (its issuing thread skips the MMAs), with
  * the barrier wait bounded to wait_limit polls instead of the default 2^26:

@@ -77,7 +77,8 @@ EXPORTS = ("cast_sv_create", "cast_sv_wrap", "cast_sv_destroy", "cast_sv_info",
            "cast_set_f64_mode", "cast_get_f64_mode", "cast_autotune", "cast_set_cost_table",
            "cast_debug_inject_timeout", "cast_measure_tensor_peak", "cast_set_sparse_mode",
            "cast_get_sparse_mode", "cast_set_c128_tensor_mode", "cast_get_c128_tensor_mode",
-           "cast_batch_create", "cast_batch_energy", "cast_batch_grad", "cast_batch_info", "cast_batch_destroy")
+           "cast_batch_create", "cast_batch_energy", "cast_batch_grad", "cast_batch_info", "cast_batch_destroy",
+           "cast_measure_mma_issue")
 
 _lib = None
 
@@ -135,6 +136,7 @@ def load(build_if_missing=True):
         "cast_set_cost_table": (I, [P]),
         "cast_debug_inject_timeout": (I, [ctypes.c_uint32]),
         "cast_measure_tensor_peak": (I, [I, P]),
+        "cast_measure_mma_issue": (I, [I, I, P]),
         "cast_set_sparse_mode": (I, [I]),
         "cast_get_sparse_mode": (I, []),
         "cast_set_c128_tensor_mode": (I, [I]),
@@ -494,6 +496,13 @@ def cast_measure_tensor_peak(kind=CAST_PEAK_TF32):
     """Measured dense tensor-pipe TFLOP/s of the current GPU (kind::tf32 or bf16)."""
     v = ctypes.c_double()
     _check(load().cast_measure_tensor_peak(int(kind), ctypes.byref(v)))
+    return float(v.value)
+
+
+def cast_measure_mma_issue(n_cols, a_in_tmem=True):
+    """SM clock cycles per back-to-back kind::f16 MMA of M = 128, K = 16, N = n_cols."""
+    v = ctypes.c_double()
+    _check(load().cast_measure_mma_issue(int(n_cols), int(bool(a_in_tmem)), ctypes.byref(v)))
     return float(v.value)
 
 

@@ -24,8 +24,9 @@
 // tensor memory, B = the stacked digits of W from shared memory, N' = blocks x
 // N) adds all of digit i's pairs at once: 7 MMAs per K-step instead of 34.
 // The MMA of i = 0 also covers a zero eighth block, so it starts every
-// accumulator.  (Measured on GB300: an M = 128, K = 16 bf16 MMA costs ~53
-// cycles for any N <= 64, 69 at N = 128, 137 at N = 256.)  Accumulator d only
+// accumulator.  (Measured on GB300 with cast_measure_mma_issue: an M = 128,
+// K = 16 bf16 MMA costs 49.5 cycles for any N <= 64, 64 at N = 128 and 128 at
+// N = 256, the last two at the bf16 peak.)  Accumulator d only
 // ever holds integers times 2^(-7d) of magnitude below (pairs of weight d) *
 // 2D * 127^2 <= 7 * 64 * 16129 < 2^23 (k <= 5), so all eight are exact in fp32
 // whatever the order of the additions or the rounding of the tensor cores.

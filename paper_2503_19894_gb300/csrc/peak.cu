@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "tc.cuh"
@@ -112,10 +113,114 @@ cast_status time_peak(int iters, double *ms) {
     return CAST_OK;
 }
 
+// Issue cost of small MMAs: thread 0 of one CTA per SM issues `iters`
+// back-to-back tcgen05.mma kind::f16 (M = 128, K = 16, N = n, bf16 zero
+// operands, A from TMEM columns 256..263 or from shared memory, one fp32
+// accumulator at column 0) and measures the SM clock from the first issue to
+// the commit's completion.
+template <bool ATMEM>
+__global__ void __launch_bounds__(128, 1) k_mma_issue(int n, int iters, long long *cycles) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;                          // 128 rows x 128 bytes
+    uint8_t *sB = sA + kPeakM * 128;             // 256 rows x 128 bytes
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sB + kPeakN * 128);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < (kPeakM + kPeakN) * 128 / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(sA)[i] = 0u;
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *tslot;
+    if (ATMEM) {  // zero A in TMEM, columns 256..263 of every lane
+        float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        tc::tmem_st<8>(taddr + (uint32_t(32 * warp) << 16) + 256u, z);
+        tc::tmem_wait_st();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(kPeakM >> 4) << 24);
+        const uint64_t da = tc::smem_desc_sw128(tc::smem_u32(sA)), db = tc::smem_desc_sw128(tc::smem_u32(sB));
+        const long long t0 = clock64();
+        for (int it = 0; it < iters; it++) {
+            if (ATMEM) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(taddr),
+                    "r"(taddr + 256u), "l"(db), "r"(idesc), "r"(1));
+            } else {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                    "l"(da), "l"(db), "r"(idesc), "r"(1));
+            }
+        }
+        tc::mma_commit(mbar);
+        if (tc::mbar_wait(mbar, 0, kPeakWait)) {
+            cycles[blockIdx.x] = clock64() - t0;
+        } else {
+            atomicOr(&g_peak_error, 1);
+            cycles[blockIdx.x] = -1;
+            tc::mbar_wait(mbar, 0, kPeakWait);  // give an MMA in flight time before TMEM is freed
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+template <bool ATMEM>
+cast_status time_mma_issue(int n, int iters, double *cycles_per_mma) {
+    const size_t smem = 1024 + (kPeakM + kPeakN) * 128 + 64 + 120 * 1024;  // > half of an SM: one CTA each
+    CAST_CUDA(cudaFuncSetAttribute(k_mma_issue<ATMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = sm_count_cached();
+    long long *d = nullptr;
+    CAST_CUDA(cudaMalloc(&d, sizeof(long long) * grid));
+    std::vector<long long> h(grid, 0);
+    cudaError_t err = cudaSuccess;
+    double best = 1e300;
+    for (int rep = 0; rep < 3 && err == cudaSuccess; rep++) {  // the first launch is a warm-up
+        k_mma_issue<ATMEM><<<grid, 128, smem>>>(n, iters, d);
+        err = cudaDeviceSynchronize();
+        if (err == cudaSuccess) err = cudaMemcpy(h.data(), d, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+        if (err == cudaSuccess && rep > 0) {
+            double sum = 0;
+            for (long long c : h) sum += double(c);
+            best = std::min(best, sum / grid / iters);
+        }
+    }
+    if (err == cudaSuccess) err = cudaGetLastError();
+    cudaFree(d);
+    if (err != cudaSuccess) return cuda_fail(err, "MMA issue kernel");
+    int flag = 0;
+    CAST_CUDA(cudaMemcpyFromSymbol(&flag, g_peak_error, sizeof(int)));
+    if (flag) {
+        const int zero = 0;
+        CAST_CUDA(cudaMemcpyToSymbol(g_peak_error, &zero, sizeof(int)));
+        return fail(CAST_ERR_TIMEOUT, "MMA issue kernel gave up waiting for its MMAs (bounded wait)");
+    }
+    *cycles_per_mma = best;
+    return CAST_OK;
+}
+
 }  // namespace
 }  // namespace cast
 
 using namespace cast;
+
+extern "C" cast_status cast_measure_mma_issue(int n_cols, int a_in_tmem, double *cycles_per_mma) {
+    if (!cycles_per_mma) return fail(CAST_ERR_ARG, "null output");
+    if (n_cols < 16 || n_cols > 256 || n_cols % 16 != 0) return fail(CAST_ERR_ARG, "N must be 16..256, a multiple of 16");
+    const int iters = 8192;
+    return a_in_tmem ? time_mma_issue<true>(n_cols, iters, cycles_per_mma)
+                     : time_mma_issue<false>(n_cols, iters, cycles_per_mma);
+}
 
 extern "C" cast_status cast_measure_tensor_peak(int kind, double *tflops) {
     if (!tflops) return fail(CAST_ERR_ARG, "null output");
