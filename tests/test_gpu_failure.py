@@ -12,9 +12,11 @@ from paper_2503_19894_gb300 import capi
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("k", [5, 6, 7])
+@pytest.mark.parametrize("k", [4, 5, 6, 7])
 def test_bounded_wait_reports_timeout_and_context_survives(k):
-    """k = 5: MMA completion barrier; k = 6, 7: also the W-chunk bulk-copy pipeline."""
+    """k = 4: the warps' hand-off barrier and the MMA completion barrier;
+    k = 5: MMA completion barrier; k = 6, 7: also the W-chunk bulk-copy
+    pipeline."""
     capi.cast_set_tensor_mode(capi.CAST_TC_TF32X3)
     n, rng = 16, np.random.default_rng(0)
     qs, u = W.sweep_targets(n, k, "mixed", rng), W.haar_unitary(k, rng)
