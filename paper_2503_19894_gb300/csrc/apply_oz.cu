@@ -12,11 +12,12 @@
 // 2^(E_r - 50), unbiased) and written as seven 7-bit digits, x = 2^E_r
 // sum_i a_i 2^(-7(i+1)), a_i in [-127, 127] (all digits carry the sign of x).  Each
 // output row n of W is split the same way with its own exponent E_n into
-// digits w_j.  Digits are stored pre-scaled, a_i 2^(-7i) and w_j 2^(-7j),
-// which bf16 represents exactly (7 significant bits times a power of two).
+// digits w_j.  For k = 3..5 the digits are stored as the integers a_i, w_j
+// themselves, for k = 6, 7 pre-scaled, a_i 2^(-7i) and w_j 2^(-7j); bf16
+// represents both exactly (7 significant bits times a power of two).
 //
 // Products.  Every pair (i, j) with i + j <= 7 contributes a_i w_j
-// 2^(-7(i+j)) to accumulator d = i + j (eight accumulators, d = 0..7).  For a
+// (weight 2^(-7(i+j))) to accumulator d = i + j (eight accumulators, d = 0..7).  For a
 // fixed digit i of X the weights i + j of j = 0, 1, ... are consecutive, so
 // with the B blocks of W's digits stacked (rows of digit 0, then digit 1, ...)
 // and the accumulators in adjacent TMEM columns, one tcgen05.mma per (i,
@@ -27,7 +28,7 @@
 // accumulator.  (Measured on GB300 with cast_measure_mma_issue: an M = 128,
 // K = 16 bf16 MMA costs 49.5 cycles for any N <= 64, 64 at N = 128 and 128 at
 // N = 256, the last two at the bf16 peak.)  Accumulator d only
-// ever holds integers times 2^(-7d) of magnitude below (pairs of weight d) *
+// ever holds integers (times 2^(-7d) when pre-scaled) of magnitude below (pairs of weight d) *
 // 2D * 127^2 <= 7 * 64 * 16129 < 2^23 (k <= 5), so all eight are exact in fp32
 // whatever the order of the additions or the rounding of the tensor cores.
 // The dropped pairs (i + j >= 8) are all of the sign of their product (every
@@ -39,13 +40,16 @@
 // against 1.5e-13 for a 2^-28 common integer scale alone: both limits are
 // gone here.
 //
-// Epilogue.  y = 2^(E_r + E_n - 14) (acc0 + ... + acc7): acc_d 2^(7d) for
-// d <= 3 are converted to integers exactly (fp32 magic-number rounding of an
-// exact integer below 2^22), acc4 * 2^28 and acc5 * 2^36 (exact integers)
-// and acc6, acc7 * 2^36 (rounded) with the conversion instruction, the eight
-// are summed in 64-bit integer arithmetic at the common scale 2^-36 and the
-// result is written as an FP64 with integer operations (leading-zero count,
-// shift, exponent), so no FP64 instruction runs on the device.
+// Epilogue.  y = 2^(E_r + E_n - 14) sum_d acc_d 2^(-7d), summed at the
+// common scale 2^-36 (in units of the weight-0 products): acc_d for d <= 3
+// are converted to integers exactly (fp32 magic-number rounding of an exact
+// integer below 2^22) and paired in 32 bits (acc0 * 2^7 + acc1, acc2 * 2^7 +
+// acc3); acc4 (an exact integer below 2^23) with the conversion instruction,
+// times 2^8, plus acc5 * 2 + acc6 * 2^-6 + acc7 * 2^-13 summed in fp32 (two
+// roundings of at most half a unit at 2^-36) and converted once; the three
+// parts are summed in 64-bit integer arithmetic and the result is written as
+// an FP64 with integer operations (leading-zero count, shift, exponent), so
+// no FP64 instruction runs on the device.
 //
 // Tensor memory holds the seven digits of A (D columns each, two bf16 per
 // column) and the eight accumulators; for k = 4, 5 the outputs are produced
@@ -54,11 +58,12 @@
 //
 // Data path: four threads per slice row (TMEM lane),
 // each with its share of the row's members.  A tile's 128 slice rows are
-// loaded with 16-byte loads into shared memory ([member][row]); the parts'
+// copied with 16-byte cp.async into shared memory ([member][row]); the parts'
 // exponents meet in shared memory; each thread forms the digits of its members once per real
 // and stores them to tensor memory with tcgen05.st; one thread issues the MMAs and
 // commits them to an mbarrier; while they run, every thread loads the next
-// tile into shared memory; the epilogue reads the eight accumulators with
+// tile into shared memory (cp.async, waited for at the next tile by the
+// thread that issued it, the only one that reads it); the epilogue reads the eight accumulators with
 // tcgen05.ld and stores the outputs.  W's digits (host-built, already in the
 // 128-byte-swizzled K-major shared-memory image) are copied in once per CTA.
 // TMEM per CTA: 7 x D digit columns + 8 x 2D / NH accumulator columns (NH
@@ -86,6 +91,20 @@ __device__ int g_oz_error;
 std::atomic<int> g_c128_tc{CAST_C128_TC_OZAKI};
 constexpr uint32_t kOzWait = 1u << 26;
 constexpr int kDigits = 7;
+// Measured per 30-qubit gate on a random state (mean of low, high and mixed
+// targets, k = 3 / 4 / 5): 17.6 / 17.3 / 22.6 ms with none of the three
+// options below, 14.7 / 14.6 / 17.6 ms with all three.
+// k = 3..5: the next tile's loads as cp.async (the threads go on to the
+// epilogue while they land) instead of loads into registers: 15.4 / 15.4 /
+// 18.6 ms alone
+constexpr bool kOzAsyncLoad = true;
+// k = 3..5: digits stored as the plain integers a_i, w_j (the weights 2^(-7d)
+// applied in the epilogue's integer shifts) instead of pre-scaled: 16.6 /
+// 16.5 / 22.0 ms alone
+constexpr bool kOzUnitDigits = true;
+// k = 3..5 with unit digits: the weights d = 5, 6, 7 summed in fp32 before
+// one conversion instead of three (16.5 / 16.3 / 21.6 ms with unit digits)
+constexpr bool kOzSumLow = true;
 
 template <int K>
 struct OzShape {
@@ -136,6 +155,11 @@ __device__ __forceinline__ Fixed49 fixed49(double x, int er) {
 __device__ __forceinline__ float digit_f(const Fixed49 &v, int i) {
     const uint32_t a = uint32_t(v.f >> (7 * (kDigits - 1 - i))) & 127u;
     return (__uint_as_float(v.mg | a) - __uint_as_float(v.mg)) * __uint_as_float(uint32_t(127 - 7 * i) << 23);
+}
+// digit i of v as the float +-a_i (exact)
+__device__ __forceinline__ float digit_u(const Fixed49 &v, int i) {
+    const uint32_t a = uint32_t(v.f >> (7 * (kDigits - 1 - i))) & 127u;
+    return __uint_as_float(v.mg | a) - __uint_as_float(v.mg);
 }
 // two such floats as one TMEM column of bf16 (lo: a, hi: b)
 __device__ __forceinline__ float bf16_pair(float a, float b) {
@@ -205,8 +229,14 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
 #pragma unroll
         for (int jj = 0; jj < DH; jj++) {
             const int j = half * DH + jj;
-            stg[j * 128 + row] = __ldcs(sv + b + member_off(j));
+            if constexpr (kOzAsyncLoad)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(stg + j * 128 + row)),
+                             "l"(sv + b + member_off(j))
+                             : "memory");
+            else
+                stg[j * 128 + row] = __ldcs(sv + b + member_off(j));
         }
+        if constexpr (kOzAsyncLoad) asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
     // kind::f16 with D fp32, A and B bf16, M = 128 (N set per MMA)
@@ -217,6 +247,8 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
     uint64_t tile = blockIdx.x;
     if (tile < ntiles) load_tile(tile);
     while (tile < ntiles) {
+        // this thread's own copies of the tile (it reads only what it loaded)
+        if constexpr (kOzAsyncLoad) asm volatile("cp.async.wait_all;" ::: "memory");
         // ---- row exponent: both halves' maxima
         int eh = -1022;
 #pragma unroll
@@ -245,7 +277,12 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
             for (int i = 0; i < kDigits; i++) {
                 float v[CH];
 #pragma unroll
-                for (int c = 0; c < CH; c++) v[c] = bf16_pair(digit_f(F[2 * c], i), digit_f(F[2 * c + 1], i));
+                for (int c = 0; c < CH; c++) {
+                    if constexpr (kOzUnitDigits)
+                        v[c] = bf16_pair(digit_u(F[2 * c], i), digit_u(F[2 * c + 1], i));
+                    else
+                        v[c] = bf16_pair(digit_f(F[2 * c], i), digit_f(F[2 * c + 1], i));
+                }
                 tc::tmem_st<CH>(lane_addr + uint32_t(i * S::DCOL + half * DH + c0), v);
             }
         }
@@ -309,14 +346,28 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
                         // common scale 2^-36 (in units of the weight-0 products): acc_d
                         // 2^(7d) is an exact integer for every d; those of d <= 5 stay
                         // exact at this scale, d = 6, 7 round to it
-                        const int64_t Y = (int64_t(exact_int(ac[0][c])) << 36) +
-                                          (int64_t(exact_int(ac[1][c] * 128.0f)) << 29) +
-                                          (int64_t(exact_int(ac[2][c] * 16384.0f)) << 22) +
-                                          (int64_t(exact_int(ac[3][c] * 2097152.0f)) << 15) +
-                                          (int64_t(__float2int_rn(ac[4][c] * 268435456.0f)) << 8) +
-                                          int64_t(__float2int_rn(ac[5][c] * 68719476736.0f)) +
-                                          int64_t(__float2int_rn(ac[6][c] * 68719476736.0f)) +
-                                          int64_t(__float2int_rn(ac[7][c] * 68719476736.0f));
+                        int64_t Y;
+                        if constexpr (kOzUnitDigits) {
+                            // acc_d holds the integer sum itself; pairs of
+                            // terms that fit 32 bits are combined first
+                            const int32_t hi = exact_int(ac[0][c]) * 128 + exact_int(ac[1][c]);
+                            const int32_t mid = exact_int(ac[2][c]) * 128 + exact_int(ac[3][c]);
+                            int32_t lo = __float2int_rn(ac[4][c]) * 256;  // |acc4| < 5 * 64 * 127^2 < 2^23
+                            if constexpr (kOzSumLow)
+                                lo += __float2int_rn(fmaf(ac[7][c], 0x1p-13f, fmaf(ac[6][c], 0x1p-6f, 2.0f * ac[5][c])));
+                            else
+                                lo += __float2int_rn(ac[5][c]) * 2 + __float2int_rn(ac[6][c] * 0x1p-6f) +
+                                      __float2int_rn(ac[7][c] * 0x1p-13f);
+                            Y = (int64_t(hi) << 29) + (int64_t(mid) << 15) + int64_t(lo);
+                        } else {
+                            Y = (int64_t(exact_int(ac[0][c])) << 36) + (int64_t(exact_int(ac[1][c] * 128.0f)) << 29) +
+                                (int64_t(exact_int(ac[2][c] * 16384.0f)) << 22) +
+                                (int64_t(exact_int(ac[3][c] * 2097152.0f)) << 15) +
+                                (int64_t(__float2int_rn(ac[4][c] * 268435456.0f)) << 8) +
+                                int64_t(__float2int_rn(ac[5][c] * 68719476736.0f)) +
+                                int64_t(__float2int_rn(ac[6][c] * 68719476736.0f)) +
+                                int64_t(__float2int_rn(ac[7][c] * 68719476736.0f));
+                        }
                         out[hh] = i64_to_double(Y, er_cur + int(P.wexp[h * NHW + col + c]) - 36);
                     }
                     const int j = ((h * NHW + col) >> 1) + m;
@@ -331,6 +382,7 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         tc::fence_before_sync();
         tile = next;
     }
+    if constexpr (kOzAsyncLoad) asm volatile("cp.async.wait_all;" ::: "memory");
     failed = __syncthreads_or(failed);
     if (failed) {
         if (tid == 0) {
@@ -746,7 +798,7 @@ uint16_t host_bf16_digit(int a, int j, bool neg) {
 // and its entries' seven digits go to img at off(n, c, j) as bf16 with the
 // sign of the entry; wexp[n] = E_n - 14.
 template <class Off>
-void build_digit_image(const PreparedGate &g, int k, std::vector<uint8_t> &img, int8_t *wexp, Off off) {
+void build_digit_image(const PreparedGate &g, int k, std::vector<uint8_t> &img, int8_t *wexp, Off off, bool unit) {
     const int D = 1 << k, NR = 2 * D;
     std::vector<double> W(size_t(NR) * NR);
     for (int r = 0; r < D; r++)
@@ -777,7 +829,7 @@ void build_digit_image(const PreparedGate &g, int k, std::vector<uint8_t> &img, 
             int dig[kDigits];
             host_digits(w, E, dig);
             for (int j = 0; j < kDigits; j++) {
-                const uint16_t b = host_bf16_digit(dig[j], j, w < 0);
+                const uint16_t b = host_bf16_digit(dig[j], unit ? 0 : j, w < 0);
                 std::memcpy(img.data() + off(n, c, j), &b, 2);
             }
         }
@@ -799,7 +851,7 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     // half n / NHW, digit block j, row n % NHW (block 7 stays zero)
     build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
         return (size_t(n / S::NHW) * S::NACC + size_t(j)) * S::NHW * 128 + sw128_bf16(n % S::NHW, c);
-    });
+    }, kOzUnitDigits);
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;
@@ -828,7 +880,7 @@ cast_status run_ozc(cast_sv *sv, const PreparedGate &g) {
     // block (pass n / 64, K-block c / 64): digit j, row n % 64, element c % 64
     build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
         return size_t((n >> 6) * S::NKB + (c >> 6)) * S::WBLK + size_t(j) * S::NHW * 128 + sw128_bf16(n & 63, c & 63);
-    });
+    }, false);
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;
@@ -856,16 +908,16 @@ bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
         g.cls != CLS_DENSE || g.k < 3 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
         return false;
-    // measured per 30-qubit gate on a random state: this kernel 16.5-19 /
-    // 16.7-18.3 / 21-24 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the
-    // list kernel matches it at about 43 / 21 / 25 / 9.5 / 4.7% of the dense
-    // operation count (it is faster below, its time growing with the
-    // operation count above a floor of 15-44 ms)
+    // measured per 30-qubit gate on a random state: this kernel 14.7 / 14.6 /
+    // 17.6 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the list kernel
+    // matches it at about 25 / 14 / 10 / 9.5 / 4.7% of the dense operation
+    // count (it is faster below, its time growing with the operation count
+    // above a floor of 15-44 ms)
     const int64_t ops = opcount(g.m.data(), g.k, 0.0), dense = dense_opcount(g.k);
     switch (g.k) {
-        case 3: return 7 * ops > 3 * dense;
-        case 4: return 9 * ops > 2 * dense;
-        case 5: return 4 * ops > dense;
+        case 3: return 4 * ops > dense;
+        case 4: return 7 * ops > dense;
+        case 5: return 10 * ops > dense;
         case 6: return 10 * ops > dense;
         default: return 20 * ops > dense;
     }
