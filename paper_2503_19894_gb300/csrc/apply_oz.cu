@@ -910,14 +910,14 @@ bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
         return false;
     // measured per 30-qubit gate on a random state: this kernel 14.7 / 14.6 /
     // 17.6 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the list kernel
-    // matches it at about 25 / 14 / 10 / 9.5 / 4.7% of the dense operation
+    // matches it at about 33 / 18 / 12.5 / 9.5 / 4.7% of the dense operation
     // count (it is faster below, its time growing with the operation count
-    // above a floor of 15-44 ms)
+    // above a floor of 13.4-14 ms for k = 3..5 and 20-44 ms for k = 6, 7)
     const int64_t ops = opcount(g.m.data(), g.k, 0.0), dense = dense_opcount(g.k);
     switch (g.k) {
-        case 3: return 4 * ops > dense;
-        case 4: return 7 * ops > dense;
-        case 5: return 10 * ops > dense;
+        case 3: return 3 * ops > dense;
+        case 4: return 11 * ops > 2 * dense;
+        case 5: return 8 * ops > dense;
         case 6: return 10 * ops > dense;
         default: return 20 * ops > dense;
     }

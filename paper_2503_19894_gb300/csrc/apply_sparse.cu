@@ -42,6 +42,12 @@ namespace {
 enum EntryKind : uint32_t { E_GEN = 0, E_RE = 1, E_IM = 2, E_P1 = 3, E_M1 = 4, E_PI = 5, E_MI = 6 };
 
 constexpr int kSpThreads = 256, kSpWarps = kSpThreads / 32, kSP = 33;  // slice-row stride of X, padded
+// The address and shared-memory slot of a thread's element u are this
+// thread's part (cube bits 0..7) plus u's part (bits 8..11, the same for every
+// thread), taken from a 16-entry table built once per CTA instead of being
+// assembled bit by bit at each of the three uses.  Measured per 30-qubit
+// complex128 gate at 6-20% density: 13.4-15.8 ms against 14.7-17.2 ms.
+constexpr bool kSpUTable = true;
 
 // Bit layout of a tile: cube position b (ascending address bit pos[b]) is
 // either bit role[b] < 16 of the slice row within the super-tile or target
@@ -226,9 +232,33 @@ k_sparse(typename A::Amp *__restrict__ sv, uint64_t nsuper, const __grid_constan
         if (r < 16) s_lo |= 1u << r;
         else j_lo |= 1u << (r - 16);
     }
-    // shared-memory slot of slice row s (g = s >> 5) and member j
+    // shared-memory slot of slice row s (g = s >> 5) and member j; linear in
+    // (s, j) for disjoint bits, so the two parts' slots add
     auto slot = [](uint32_t s, uint32_t j) { return ((s >> 5) * D + j) * kSP + (s & 31); };
+    __shared__ uint4 sU[PER];  // u's part: address (lo, hi), slot
+    if constexpr (kSpUTable) {
+        if (tid < PER) {
+            uint64_t a = 0;
+            uint32_t s = 0, j = 0;
+            for (int b = 8; b < 12; b++) {
+                if (!((tid >> (b - 8)) & 1)) continue;
+                a += uint64_t(1) << lay.pos[b];
+                const int r = lay.role[b];
+                if (r < 16) s |= 1u << r;
+                else j |= 1u << (r - 16);
+            }
+            sU[tid] = make_uint4(uint32_t(a), uint32_t(a >> 32), slot(s, j), 0u);
+        }
+        __syncthreads();
+    }
+    const uint32_t sl_lo = slot(s_lo, j_lo);
     auto elem = [&](int u, uint64_t &a, uint32_t &sl) {
+        if constexpr (kSpUTable) {
+            const uint4 t = sU[u];
+            a = a_lo + (uint64_t(t.y) << 32 | t.x);
+            sl = sl_lo + t.z;
+            return;
+        }
         a = a_lo;
         uint32_t s = s_lo, j = j_lo;
 #pragma unroll
