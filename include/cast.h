@@ -134,7 +134,7 @@ int cast_get_tensor_mode(void);
  *     and cut to 49 fractional bits (rounded), the digit-pair products with
  *     i + j <= 7 are accumulated by weight, and the result is assembled with
  *     integer operations; error ~2^-48 of the slice's largest amplitude.
- *     Gates below about 33 / 18 / 12 / 10 / 5% of the dense operation count
+ *     Gates below about 33 / 17 / 11 / 10 / 5% of the dense operation count
  *     (k = 3..7), where the list kernel is faster, stay on it.  The paper has
  *     no tensor-core path; this is the complex128 form of Eq. 3's matvec on
  *     GB300's tensor cores.

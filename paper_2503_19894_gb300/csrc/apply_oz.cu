@@ -92,8 +92,9 @@ std::atomic<int> g_c128_tc{CAST_C128_TC_OZAKI};
 constexpr uint32_t kOzWait = 1u << 26;
 constexpr int kDigits = 7;
 // Measured per 30-qubit gate on a random state (mean of low, high and mixed
-// targets, k = 3 / 4 / 5): 17.6 / 17.3 / 22.6 ms with none of the three
-// options below, 14.7 / 14.6 / 17.6 ms with all three.
+// targets, k = 3 / 4 / 5): 17.6 / 17.3 / 22.6 ms with none of the four
+// options below, 14.7 / 14.6 / 17.6 ms with the first three, 14.2 / 14.1 /
+// 16.3 ms with all four.
 // k = 3..5: the next tile's loads as cp.async (the threads go on to the
 // epilogue while they land) instead of loads into registers: 15.4 / 15.4 /
 // 18.6 ms alone
@@ -105,6 +106,12 @@ constexpr bool kOzUnitDigits = true;
 // k = 3..5 with unit digits: the weights d = 5, 6, 7 summed in fp32 before
 // one conversion instead of three (16.5 / 16.3 / 21.6 ms with unit digits)
 constexpr bool kOzSumLow = true;
+// k = 3..5: two CTA barriers per tile left out. The one before the next
+// tile's loads guarded nothing (each thread reloads only the staged rows it
+// read itself, and the exponents are read before the MMA barrier); the one
+// after the last output half's epilogue is implied by the next tile's
+// barriers, which every thread reaches only after its epilogue.
+constexpr bool kOzFewBarriers = true;
 
 template <int K>
 struct OzShape {
@@ -322,7 +329,7 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
             __syncwarp();
             if (h == 0) {
                 // ---- the next tile's loads run while the MMAs execute
-                __syncthreads();  // every thread has read the staged tile and the exponents
+                if constexpr (!kOzFewBarriers) __syncthreads();
                 if (next < ntiles) load_tile(next);
             }
             failed = __syncthreads_or(!tc::mbar_wait(mbar, phase, wait_limit));  // agreed by all threads
@@ -375,7 +382,9 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
                 }
             }
             tc::fence_before_sync();
-            __syncthreads();  // the accumulators are read before the next MMAs overwrite them
+            // the accumulators are read before the next MMAs overwrite them (the
+            // next tile's MMAs wait at that tile's barriers)
+            if (!kOzFewBarriers || h + 1 < S::NH) __syncthreads();
             tc::fence_after_sync();
         }
         if (failed) break;
@@ -908,16 +917,16 @@ bool oz_eligible(const cast_sv *sv, const PreparedGate &g) {
     if (g_c128_tc.load() != CAST_C128_TC_OZAKI || f64_mode() != CAST_F64_EMULATED || sv->dt != CAST_C128 ||
         g.cls != CLS_DENSE || g.k < 3 || sv->n < g.k + 7 || sparse_mode() == CAST_SPARSE_ALWAYS)
         return false;
-    // measured per 30-qubit gate on a random state: this kernel 14.7 / 14.6 /
-    // 17.6 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the list kernel
-    // matches it at about 33 / 18 / 12.5 / 9.5 / 4.7% of the dense operation
+    // measured per 30-qubit gate on a random state: this kernel 14.2 / 14.1 /
+    // 16.3 / 30-32 / 52-53 ms (k = 3..7) whatever the matrix; the list kernel
+    // matches it at about 33 / 17 / 11 / 9.5 / 4.7% of the dense operation
     // count (it is faster below, its time growing with the operation count
     // above a floor of 13.4-14 ms for k = 3..5 and 20-44 ms for k = 6, 7)
     const int64_t ops = opcount(g.m.data(), g.k, 0.0), dense = dense_opcount(g.k);
     switch (g.k) {
         case 3: return 3 * ops > dense;
-        case 4: return 11 * ops > 2 * dense;
-        case 5: return 8 * ops > dense;
+        case 4: return 6 * ops > dense;
+        case 5: return 9 * ops > dense;
         case 6: return 10 * ops > dense;
         default: return 20 * ops > dense;
     }

@@ -160,7 +160,7 @@ def test_oz_fused_circuits(fam, fusion, max_k, oz_mode):
 
 
 def test_oz_sparse_gates_stay_on_the_sparse_kernel(oz_mode):
-    k, n = 5, 13  # two entries per row: 3% of the dense count, below the 12.5% crossover (5% for k = 7)
+    k, n = 5, 13  # two entries per row: 3% of the dense count, below the 11% crossover (5% for k = 7)
     d = 1 << k
     m = np.zeros((d, d), dtype=np.complex128)
     for r in range(d):
