@@ -190,7 +190,9 @@ cast_status cast_measure_tensor_peak(int kind, double *tflops);
  * CAST_ERR_ARG unless n_cols is 16..256 and a multiple of 16. */
 cast_status cast_measure_mma_issue(int n_cols, int a_in_tmem, double *cycles_per_mma);
 
-/* Failure-detection test hook.  The next tensor-core gate launch waits on an
+/* Failure-detection test hook.  The next tensor-core gate launch (complex64
+ * k = 4..7, complex128 digit products k = 3..5; a complex128 gate of k = 6,
+ * 7 leaves the hook pending) waits on an
  * MMA completion that never comes (its issuing thread skips the MMAs), with
  * the barrier wait bounded to wait_limit polls instead of the default 2^26:
  * every CTA gives up, frees its tensor memory and returns; the error is

@@ -193,7 +193,8 @@ __device__ __forceinline__ double i64_to_double(int64_t Y, int e) {
 template <int K>
 __global__ void __launch_bounds__(OzShape<K>::NT, OzShape<K>::MIN_CTAS)
 k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Targets tg,
-           const uint8_t *__restrict__ wimg, const __grid_constant__ OzParams P, uint32_t wait_limit) {
+           const uint8_t *__restrict__ wimg, const __grid_constant__ OzParams P, uint32_t wait_limit,
+           int skip_mma) {
     using S = OzShape<K>;
     constexpr int D = S::D, NHW = S::NHW, NACC = S::NACC;
     constexpr int R = S::R, NT = S::NT;
@@ -302,7 +303,9 @@ k_dense_oz(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ Ta
         const uint64_t ob = slice_base<K>(tile * 128 + row, tg);
 #pragma unroll
         for (int h = 0; h < S::NH; h++) {
-            if (tid == 0) {
+            // (skip_mma: failure-detection test hook, no MMA and no commit, so
+            // every thread's bounded wait below runs out)
+            if (tid == 0 && !skip_mma) {
                 // one MMA per (A digit i, K-step): the B blocks of digits j = 0.. are
                 // stacked rows, and the accumulators of weights d = i + j adjacent
                 // columns, so N' = (blocks) x NHW covers accumulators i..7 at once.
@@ -874,8 +877,10 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     const uint64_t grid = ntiles < cap ? ntiles : cap;
     const double N = double(uint64_t(1) << sv->n);
     ProfScope ps(sv->stream, "ozdense_k" + std::to_string(K) + "_c128", 32.0 * N, 8.0 * N * double(D));
+    const uint32_t inject = take_inject_limit();
     k_dense_oz<K><<<(unsigned)grid, S::NT, smem, sv->stream>>>(reinterpret_cast<double2 *>(sv->data), ntiles, tg,
-                                                             static_cast<const uint8_t *>(dev), P, kOzWait);
+                                                             static_cast<const uint8_t *>(dev), P,
+                                                             inject ? inject : kOzWait, inject ? 1 : 0);
     CAST_CUDA(cudaGetLastError());
     return CAST_OK;
 }

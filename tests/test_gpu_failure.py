@@ -39,3 +39,30 @@ def test_bounded_wait_reports_timeout_and_context_survives(k):
 def test_inject_rejects_zero_limit():
     with pytest.raises(capi.CastError):
         capi.cast_debug_inject_timeout(0)
+
+
+def test_bounded_wait_in_the_complex128_digit_kernel():
+    """The complex128 digit kernel (k = 4, MMA completion barrier): the same
+    hook, the same report, and the next gate on the same state is exact."""
+    old = capi.cast_get_c128_tensor_mode()
+    capi.cast_set_c128_tensor_mode(capi.CAST_C128_TC_OZAKI)
+    try:
+        n, rng = 16, np.random.default_rng(1)
+        qs, u = W.sweep_targets(n, 4, "mixed", rng), W.haar_unitary(4, rng)
+        sv = pkg.StateVector(n, "c128")
+        capi.cast_debug_inject_timeout(1 << 12)
+        capi.cast_profile_begin()
+        sv.apply_gate(qs, u)
+        with pytest.raises(capi.CastError) as e:
+            sv.to_numpy()
+        assert e.value.status == 4 and "bounded wait" in str(e.value)
+        assert [p["name"] for p in capi.cast_profile_end()] == ["ozdense_k4_c128"]
+        sv.set_basis(0)
+        psi0 = W.random_state(n, 3)
+        sv.from_numpy(psi0)
+        sv.apply_gate(qs, u)
+        ref = oracle.apply_gate(psi0.copy(), qs, u)
+        assert np.max(np.abs(sv.to_numpy() - ref)) <= 1e-12
+        sv.close()
+    finally:
+        capi.cast_set_c128_tensor_mode(old)
