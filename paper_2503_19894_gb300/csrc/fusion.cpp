@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <set>
+#include <utility>
 
 #include "internal.h"
 
@@ -49,31 +51,81 @@ struct Tile {
     std::vector<std::vector<int>> rows;  // rows[r][q] = block id or -1
 };
 
-// y = lift(U on positions pos) * M, columnwise; M is ku-qubit (2^ku x 2^ku).
+// Offsets of the 2^k member indices of a gate on positions pos (bit i of j
+// sets bit pos[i]).
+std::vector<size_t> member_offsets(const std::vector<int> &pos) {
+    const size_t dk = size_t(1) << pos.size();
+    std::vector<size_t> off(dk, 0);
+    for (size_t j = 0; j < dk; j++)
+        for (size_t i = 0; i < pos.size(); i++)
+            if ((j >> i) & 1) off[j] |= size_t(1) << pos[i];
+    return off;
+}
+
+// M <- lift(U on positions pos) * M; M is ku-qubit (2^ku x 2^ku).  The rows
+// of M fall into groups of 2^k that differ only at pos; each group is
+// replaced by U times it, whole rows at a time (contiguous in memory).  Every
+// output entry sums its products in the order of U's columns, skipping zero
+// entries of U (their products add nothing).
 void left_apply(std::vector<cplx> &M, int ku, const std::vector<cplx> &U, const std::vector<int> &pos) {
-    const int k = (int)pos.size();
-    const size_t du = size_t(1) << ku, dk = size_t(1) << k;
-    uint64_t tmask = 0;
-    for (int p : pos) tmask |= uint64_t(1) << p;
-    std::vector<cplx> x(dk);
-    std::vector<size_t> idx(dk);
-    for (size_t col = 0; col < du; col++) {
-        for (size_t b = 0; b < du; b++) {
-            if (b & tmask) continue;
-            for (size_t j = 0; j < dk; j++) {
-                size_t a = b;
-                for (int i = 0; i < k; i++)
-                    if ((j >> i) & 1) a |= size_t(1) << pos[i];
-                idx[j] = a;
-                x[j] = M[a * du + col];
-            }
-            for (size_t r = 0; r < dk; r++) {
-                cplx acc(0.0, 0.0);
-                for (size_t c = 0; c < dk; c++) acc += U[r * dk + c] * x[c];
-                M[idx[r] * du + col] = acc;
+    const size_t du = size_t(1) << ku, dk = size_t(1) << pos.size();
+    const std::vector<size_t> off = member_offsets(pos);
+    const size_t tmask = off[dk - 1];
+    std::vector<cplx> rows(dk * du);
+    for (size_t b = 0; b < du; b++) {
+        if (b & tmask) continue;
+        for (size_t j = 0; j < dk; j++) std::copy_n(&M[(b + off[j]) * du], du, &rows[j * du]);
+        for (size_t r = 0; r < dk; r++) {
+            cplx *out = &M[(b + off[r]) * du];
+            std::fill_n(out, du, cplx(0.0, 0.0));
+            for (size_t c = 0; c < dk; c++) {
+                const cplx u = U[r * dk + c];
+                if (u == cplx(0.0, 0.0)) continue;
+                const cplx *x = &rows[c * du];
+                for (size_t col = 0; col < du; col++) out[col] += u * x[col];
             }
         }
     }
+}
+
+// M <- M * lift(U on positions pos), the same way by columns: in every row,
+// the 2^k entries that differ only at pos are replaced by their product
+// with U (sums in the order of U's rows, zero entries skipped).
+void right_apply(std::vector<cplx> &M, int ku, const std::vector<cplx> &U, const std::vector<int> &pos) {
+    const size_t du = size_t(1) << ku, dk = size_t(1) << pos.size();
+    const std::vector<size_t> off = member_offsets(pos);
+    const size_t tmask = off[dk - 1];
+    std::vector<cplx> x(dk), y(dk);
+    for (size_t r = 0; r < du; r++) {
+        cplx *row = &M[r * du];
+        for (size_t b = 0; b < du; b++) {
+            if (b & tmask) continue;
+            for (size_t c = 0; c < dk; c++) x[c] = row[b + off[c]];
+            std::fill(y.begin(), y.end(), cplx(0.0, 0.0));
+            for (size_t c = 0; c < dk; c++) {
+                if (x[c] == cplx(0.0, 0.0)) continue;
+                const cplx *u = &U[c * dk];
+                for (size_t j = 0; j < dk; j++)
+                    if (u[j] != cplx(0.0, 0.0)) y[j] += x[c] * u[j];
+            }
+            for (size_t j = 0; j < dk; j++) row[b + off[j]] = y[j];
+        }
+    }
+}
+
+// lift(U on positions pos) as a ku-qubit matrix: entry (r, c) is U's entry of
+// their member bits where r and c agree at every other position, else 0
+std::vector<cplx> lift(int ku, const std::vector<cplx> &U, const std::vector<int> &pos) {
+    const size_t du = size_t(1) << ku;
+    std::vector<cplx> M(du * du, cplx(0.0, 0.0));
+    const std::vector<size_t> off = member_offsets(pos);
+    const size_t dk = off.size(), mask = off[dk - 1];
+    for (size_t b = 0; b < du; b++) {
+        if (b & mask) continue;
+        for (size_t r = 0; r < dk; r++)
+            for (size_t c = 0; c < dk; c++) M[(b + off[r]) * du + b + off[c]] = U[r * dk + c];
+    }
+    return M;
 }
 
 std::vector<int> union_q(const Block &a, const Block &b) {
@@ -93,11 +145,15 @@ Block product(const Block &first, const Block &second, double tol) {
     Block f;
     f.q = union_q(first, second);
     const int ku = (int)f.q.size();
-    const size_t du = size_t(1) << ku;
-    f.m.assign(du * du, cplx(0.0, 0.0));
-    for (size_t i = 0; i < du; i++) f.m[i * du + i] = 1.0;
-    left_apply(f.m, ku, first.m, positions(first.q, f.q));
-    left_apply(f.m, ku, second.m, positions(second.q, f.q));
+    // second * first on the union: lift the larger block and apply the
+    // smaller one to it (2^(2 ku) times the smaller dimension operations)
+    if (second.q.size() <= first.q.size()) {
+        f.m = lift(ku, first.m, positions(first.q, f.q));
+        left_apply(f.m, ku, second.m, positions(second.q, f.q));
+    } else {
+        f.m = lift(ku, second.m, positions(second.q, f.q));
+        right_apply(f.m, ku, first.m, positions(first.q, f.q));
+    }
     f.ops = opcount(f.m.data(), ku, tol);
     return f;
 }
@@ -108,6 +164,10 @@ struct Fuser {
     std::vector<Block> blocks;
     std::vector<char> alive;
     Tile T;
+    // pairs (first, second) the cost test refused: blocks never change (a
+    // fusion makes a new block), and the test does not depend on the size
+    // limit, so a later traversal refuses them again without the product
+    std::set<std::pair<int, int>> refused;
 
     int64_t cost(const Block &b) const {
         const int k = (int)b.q.size();
@@ -151,10 +211,12 @@ struct Fuser {
         if ((int)union_q(a, b).size() > k) return false;
         // consecutive: a (upper row) acts first; commuting: disjoint, any order
         (void)consecutive;
+        const bool adaptive = opt.fusion == CAST_FUSE_ADAPTIVE;
+        if (adaptive && refused.count({top, bot})) return false;
         *out = product(a, b, opt.zero_tol);
-        if (opt.fusion == CAST_FUSE_ADAPTIVE) {
-            if (out->ops > opt.op_cap) return false;
-            if (cost(*out) > cost(a) + cost(b)) return false;
+        if (adaptive && (out->ops > opt.op_cap || cost(*out) > cost(a) + cost(b))) {
+            refused.insert({top, bot});
+            return false;
         }
         return true;
     }
@@ -220,14 +282,17 @@ struct Fuser {
         T.rows.swap(kept);
     }
 
+    // one size of the schedule: traverse until nothing fuses
+    void grow(int k) {
+        while (traverse(k)) compress();
+        compress();
+    }
+
     void run() {
         if (opt.fusion == CAST_FUSE_NONE) return;
         const int kmax = opt.max_k;
         const int k0 = opt.agglomerative ? std::min(2, kmax) : kmax;
-        for (int k = k0; k <= kmax; k++) {
-            while (traverse(k)) compress();
-            compress();
-        }
+        for (int k = k0; k <= kmax; k++) grow(k);
     }
 };
 
@@ -249,35 +314,10 @@ int64_t default_amp_ops_per_pass(cast_dtype dt) {
     return f64_mode() == CAST_F64_EMULATED ? 64 : 2;
 }
 
-static cast_status fuse_once(const cast_circuit *c, const double *params, const cast_options *opt,
-                             std::vector<FusedGate> *out);
+namespace {
 
-// With a cost table and max_k = 0, try every fusion width and keep the plan of
-// least estimated time (ties: the smaller width).
-cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast_options *opt,
-                         std::vector<FusedGate> *out) {
-    if (!(opt->cost && opt->max_k == 0)) return fuse_once(c, params, opt, out);
-    int64_t best = -1;
-    for (int k = 2; k <= CAST_MAX_K; k++) {
-        cast_options o = *opt;
-        o.max_k = k;
-        std::vector<FusedGate> cand;
-        cast_status st = fuse_once(c, params, &o, &cand);
-        if (st != CAST_OK) return st;
-        int64_t total = 0;
-        for (const FusedGate &g : cand)
-            total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol), g.ops);
-        if (best < 0 || total < best) {
-            best = total;
-            out->swap(cand);
-        }
-    }
-    return CAST_OK;
-}
-
-static cast_status fuse_once(const cast_circuit *c, const double *params, const cast_options *opt,
-                             std::vector<FusedGate> *out) {
-    Fuser F{*opt, opt->amp_ops_per_pass > 0 ? opt->amp_ops_per_pass : default_amp_ops_per_pass(CAST_C64), {}, {}, {c->n_qubits, {}}};
+// The circuit's gates as the first blocks of F, in order.
+cast_status load_circuit(const cast_circuit *c, const double *params, const cast_options *opt, Fuser &F) {
     for (int g = 0; g < c->n_gates; g++) {
         const cast_gate &gt = c->gates[g];
         std::vector<cplx> m;
@@ -292,7 +332,11 @@ static cast_status fuse_once(const cast_circuit *c, const double *params, const 
         b.ops = opcount(b.m.data(), pg.k, opt->zero_tol);
         F.append(std::move(b));
     }
-    F.run();
+    return CAST_OK;
+}
+
+// The current blocks in plan order: rows top to bottom, each row by qubit.
+void emit(const Fuser &F, std::vector<FusedGate> *out) {
     out->clear();
     std::vector<char> emitted(F.blocks.size(), 0);
     for (auto &row : F.T.rows)
@@ -308,6 +352,64 @@ static cast_status fuse_once(const cast_circuit *c, const double *params, const 
             fg.ops = b.ops;
             out->push_back(std::move(fg));
         }
+}
+
+int64_t amp_ops_per_pass(const cast_options *opt) {
+    return opt->amp_ops_per_pass > 0 ? opt->amp_ops_per_pass : default_amp_ops_per_pass(CAST_C64);
+}
+
+}  // namespace
+
+// With a cost table and max_k = 0, try every fusion width and keep the plan of
+// least estimated time (ties: the smaller width).  The agglomerative
+// schedule of width w is that of width w - 1 followed by one more size, so
+// one schedule grown to the largest width yields every candidate plan.
+cast_status fuse_circuit(const cast_circuit *c, const double *params, const cast_options *opt,
+                         std::vector<FusedGate> *out) {
+    const bool search = opt->cost && opt->max_k == 0;
+    if (!search || !opt->agglomerative || opt->fusion == CAST_FUSE_NONE) {
+        int64_t best = -1;
+        for (int k = search ? 2 : opt->max_k; k <= (search ? CAST_MAX_K : opt->max_k); k++) {
+            cast_options o = *opt;
+            o.max_k = k;
+            Fuser F{o, amp_ops_per_pass(opt), {}, {}, {c->n_qubits, {}}};
+            cast_status st = load_circuit(c, params, opt, F);
+            if (st != CAST_OK) return st;
+            F.run();
+            std::vector<FusedGate> cand;
+            emit(F, &cand);
+            if (!search) {
+                out->swap(cand);
+                return CAST_OK;
+            }
+            int64_t total = 0;
+            for (const FusedGate &g : cand)
+                total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol), g.ops);
+            if (best < 0 || total < best) {
+                best = total;
+                out->swap(cand);
+            }
+        }
+        return CAST_OK;
+    }
+    cast_options o = *opt;
+    o.max_k = CAST_MAX_K;
+    Fuser F{o, amp_ops_per_pass(opt), {}, {}, {c->n_qubits, {}}};
+    cast_status st = load_circuit(c, params, opt, F);
+    if (st != CAST_OK) return st;
+    int64_t best = -1;
+    for (int k = 2; k <= CAST_MAX_K; k++) {
+        F.grow(k);
+        std::vector<FusedGate> cand;
+        emit(F, &cand);
+        int64_t total = 0;
+        for (const FusedGate &g : cand)
+            total += table_estimate(*opt->cost, g.k, classify_matrix(g.m.data(), g.k, o.zero_tol), g.ops);
+        if (best < 0 || total < best) {
+            best = total;
+            out->swap(cand);
+        }
+    }
     return CAST_OK;
 }
 
