@@ -8,7 +8,7 @@
 //   split  FP64 -> (hi, lo): hi keeps the top 24 significand bits; lo is the
 //          next 23, formed as t - 2^(E-23) where t carries the same exponent
 //          as the subtracted power of two (an exact FP32 subtraction).  The
-//          six lowest bits are dropped: |x - hi - lo| < 2^-47 |x|.  Values
+//          six lowest bits are dropped: |x - hi - lo| < 2^-46 |x|.  Values
 //          below 2^-100 in magnitude become 0 (an absolute error < 1e-30).
 //   join   (hi, lo) -> FP64: the pair is renormalised (TwoSum) and both
 //          significands are placed into one 53-bit integer significand.
