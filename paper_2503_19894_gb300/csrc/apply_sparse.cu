@@ -49,14 +49,6 @@ constexpr int kSpThreads = 256, kSpWarps = kSpThreads / 32, kSP = 33;  // slice-
 // complex128 gate at 6-20% density: 13.4-15.8 ms against 14.7-17.2 ms.
 constexpr bool kSpUTable = true;
 
-// Bit layout of a tile: cube position b (ascending address bit pos[b]) is
-// either bit role[b] < 16 of the slice row within the super-tile or target
-// bit role[b] - 16 of the member index.
-struct SpTile {
-    uint8_t pos[12];
-    uint8_t role[12];
-};
-
 // ------------------------------------------------------------ arithmetic
 // apply<G>: y[g] += u * x[g] for G slices at once (one entry decode serves
 // all of them); x[g] = xs[g * gs].
@@ -360,26 +352,6 @@ uint32_t entry_kind(cplx u) {
     if (u.imag() == 0.0) return E_RE;
     if (u.real() == 0.0) return E_IM;
     return E_GEN;
-}
-
-SpTile make_tile_layout(const int *q, int k) {
-    // 12 cube bits: the 12 - k lowest non-target positions (slice row bits)
-    // and the k targets, ascending
-    SpTile t{};
-    int nb = 0, nr = 0;
-    for (int a = 0; nb < 12; a++) {
-        int ti = -1;
-        for (int i = 0; i < k; i++)
-            if (q[i] == a) ti = i;
-        if (ti >= 0) {
-            t.pos[nb] = (uint8_t)a;
-            t.role[nb++] = (uint8_t)(16 + ti);
-        } else if (nr < 12 - k) {
-            t.pos[nb] = (uint8_t)a;
-            t.role[nb++] = (uint8_t)nr++;
-        }
-    }
-    return t;
 }
 
 template <class A, int K>

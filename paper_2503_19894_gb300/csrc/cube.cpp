@@ -1,7 +1,8 @@
 // Host-built staging tables of a warp's cube (struct CubeTables in
 // internal.h): the gather of Eq. 3 for 32 consecutive slices, laid out so that
 // the warp moves it between HBM and shared memory with coalesced 16-byte
-// chunks and every lane then reads its own slice row.
+// chunks and every lane then reads its own slice row.  Also the bit layout of
+// the list kernel's 4096-amplitude super-tiles (struct SpTile).
 #include "internal.h"
 
 namespace cast {
@@ -76,6 +77,26 @@ CubeTables make_cube_tables(const int *q, int k, int mb) {
     for (int m = 0; m < 16; m++) ct.s_mem[m] = m < (1 << mb) ? slot(deposit(uint32_t(m), mpos, mb)) : 0;
     ct.pair = (k >= 1 && q[0] == 0) ? 1u : 0u;
     return ct;
+}
+
+SpTile make_tile_layout(const int *q, int k) {
+    // 12 cube bits: the 12 - k lowest non-target positions (slice row bits)
+    // and the k targets, ascending
+    SpTile t{};
+    int nb = 0, nr = 0;
+    for (int a = 0; nb < 12; a++) {
+        int ti = -1;
+        for (int i = 0; i < k; i++)
+            if (q[i] == a) ti = i;
+        if (ti >= 0) {
+            t.pos[nb] = (uint8_t)a;
+            t.role[nb++] = (uint8_t)(16 + ti);
+        } else if (nr < 12 - k) {
+            t.pos[nb] = (uint8_t)a;
+            t.role[nb++] = (uint8_t)nr++;
+        }
+    }
+    return t;
 }
 
 }  // namespace cast

@@ -168,6 +168,18 @@ CubeTables make_cube_tables(const int *q, int k);
 // the same with the cube's member bits given: the first mb targets (mb <= min(k, 4))
 CubeTables make_cube_tables(const int *q, int k, int mb);
 
+// Bit layout of a list-kernel super-tile (apply_sparse.cu): 4096 amplitudes
+// whose 12 varying address bits are the 12 - k lowest non-target positions
+// and the k targets.  Cube position b (ascending address bit pos[b]) is
+// either bit role[b] < 16 of the slice row within the super-tile or target
+// bit role[b] - 16 of the member index.  Built on the host per gate
+// (csrc/cube.cpp); needs n >= 12.
+struct SpTile {
+    uint8_t pos[12];
+    uint8_t role[12];
+};
+SpTile make_tile_layout(const int *q, int k);
+
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);

@@ -28,3 +28,21 @@ def test_cube_tables(tmp_path):
     assert int(fields["worst_row(q0==0)"]) <= 2
     assert fields["worst_chunk"] == "1"
     assert fields["worst_pair"] == "1"
+
+
+def test_sparse_super_tile_layout(tmp_path):
+    """The list kernel's super-tile mapping (make_tile_layout plus the
+    kernel's per-thread and per-element offsets): 4096 distinct amplitudes,
+    each the one Eq. 3 gathers for its slot, and 4096 distinct slots, for
+    3000 random gates (tests/native/sparse_layout_check.cpp)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path / "sparse_layout_check")
+    cmd = [gxx, "-O2", "-std=c++17", "-I", CSRC, "-I", "/usr/local/cuda/include",
+           os.path.join(ROOT, "tests", "native", "sparse_layout_check.cpp"), os.path.join(CSRC, "cube.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    fields = dict(kv.split("=", 1) for kv in out.stdout.split())
+    assert fields["bad"] == "0" and int(fields["checked"]) == 9000
