@@ -323,8 +323,7 @@ def verify_results(n, dtype, x, qft, rqc, max_k, zval, slices=16):
     import paper_2503_19894_gb300 as pkg
     from paper_2503_19894_gb300 import capi
     S = 8 if dtype == "c64" else 16
-    P = 82 if S == 8 else (16 if capi.cast_get_f64_mode() == capi.CAST_F64_EMULATED else 2)
-    opts = capi.options("adaptive", max_k, amp_ops_per_pass=P)
+    opts = capi.options("adaptive", max_k)  # the timed step's options: the same plans
     out = {"bound_abs": 1e-5 if S == 8 else 1e-12}
     sv = pkg.StateVector(n, dtype, init_index=x)
     pq = capi.cast_plan_create(n, qft, opts=opts, dtype=dtype)

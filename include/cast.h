@@ -289,6 +289,10 @@ typedef struct {
                                     with max_k = 0 the plan also picks the fusion width
                                     2..CAST_MAX_K of least estimated time.  NULL = model */
 } cast_options;
+/* Every call taking options returns CAST_ERR_ARG, before any other work, for
+ * an unknown fusion mode, max_k outside 1..CAST_MAX_K (0 only with a cost
+ * table), agglomerative other than 0 or 1, a negative or non-finite
+ * zero_tol, a negative op_cap or a negative amp_ops_per_pass. */
 
 /* Measure the cost table on a scratch state of n_qubits (allocated and
  * freed here, filled with seeded pseudo-random amplitudes so that kernels

@@ -336,7 +336,7 @@ static cast_options resolve_options(const cast_options *opt, cast_dtype dt) {
         o = *opt;
     else
         cast_options_default(&o);
-    if (o.amp_ops_per_pass <= 0) o.amp_ops_per_pass = (int32_t)default_amp_ops_per_pass(dt);
+    if (o.amp_ops_per_pass == 0) o.amp_ops_per_pass = (int32_t)default_amp_ops_per_pass(dt);
     return o;
 }
 
@@ -345,6 +345,9 @@ static cast_status check_options(const cast_options &o) {
     if (o.max_k < (o.cost ? 0 : 1) || o.max_k > CAST_MAX_K)
         return fail(CAST_ERR_ARG, "max_k must be in 1..7 (0 = chosen from a cost table)");
     if (!(o.zero_tol >= 0.0) || !std::isfinite(o.zero_tol)) return fail(CAST_ERR_ARG, "bad zero_tol");
+    if (o.op_cap < 0) return fail(CAST_ERR_ARG, "op_cap must be >= 0");
+    if (o.amp_ops_per_pass < 0) return fail(CAST_ERR_ARG, "amp_ops_per_pass must be >= 0 (0 = default)");
+    if (o.agglomerative != 0 && o.agglomerative != 1) return fail(CAST_ERR_ARG, "agglomerative must be 0 or 1");
     return CAST_OK;
 }
 

@@ -202,3 +202,17 @@ def test_plan_default_cost_constant_follows_the_state_type():
         assert info("c128", 2)[0] > info("c128", 64)[0]
     finally:
         capi.cast_set_f64_mode(old)
+
+
+def test_options_are_validated():
+    """Negative caps and constants and a non-boolean schedule flag are refused
+    before any work; zero keeps its documented meaning (the default
+    constant)."""
+    gates = [W.Gate("H", (0,)), W.Gate("CX", (0, 1))]
+    for kw in (dict(op_cap=-1), dict(amp_ops_per_pass=-5), dict(zero_tol=-1.0)):
+        assert _err(lambda: capi.cast_fuse(3, gates, opts=capi.options("adaptive", 3, **kw))) == 1
+    o = capi.options("adaptive", 3)
+    o.agglomerative = 2
+    assert _err(lambda: capi.cast_fuse(3, gates, opts=o)) == 1
+    assert len(capi.cast_fuse(3, gates, opts=capi.options("adaptive", 3, amp_ops_per_pass=0))) == 1
+    assert len(capi.cast_fuse(3, gates, opts=capi.options("adaptive", 3, op_cap=0))) == 2
