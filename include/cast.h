@@ -67,7 +67,8 @@ cast_status cast_sv_create(int n_qubits, cast_dtype dt, void *cuda_stream, cast_
 /* Wrap caller-owned device memory (2^n_qubits amplitudes of type dt, 256-byte
  * aligned) without copying it; the contents are used as they are.  The
  * caller keeps ownership and must keep the memory alive until
- * cast_sv_destroy(*out). */
+ * cast_sv_destroy(*out).  CAST_ERR_ARG for a NULL or misaligned pointer or
+ * n_qubits outside 1..CAST_MAX_QUBITS. */
 cast_status cast_sv_wrap(void *device_ptr, int n_qubits, cast_dtype dt, void *cuda_stream,
                          cast_sv **out);
 
@@ -78,11 +79,14 @@ cast_status cast_sv_destroy(cast_sv *sv);
 /* Size and location of a state. Any out-pointer may be NULL. */
 cast_status cast_sv_info(const cast_sv *sv, int *n_qubits, cast_dtype *dt, void **device_ptr);
 
-/* Set the state to the computational basis state |index>, index < 2^n. */
+/* Set the state to the computational basis state |index>, index < 2^n.
+ * CAST_ERR_ARG for a NULL state or index >= 2^n. */
 cast_status cast_sv_set_basis(cast_sv *sv, uint64_t index);
 
 /* Copy all 2^n amplitudes to / from host memory (2^n * S bytes, interleaved).
- * Both wait for completion before returning. */
+ * Both wait for completion before returning.  CAST_ERR_ARG for a NULL state
+ * or buffer; copy_to_host also reports a bounded device wait that gave up in
+ * earlier work on the stream (CAST_ERR_TIMEOUT). */
 cast_status cast_sv_copy_to_host(const cast_sv *sv, void *host);
 cast_status cast_sv_copy_from_host(cast_sv *sv, const void *host);
 
@@ -104,7 +108,9 @@ cast_status cast_sv_copy_from_host_async(cast_sv *sv, const void *host);
  * target bits, multiply by the 2^k x 2^k matrix, scatter back (Eq. 3).
  * qubits: k distinct values in [0, n).  matrix: 4^k complex128 entries.
  * Entries with |re|, |im| <= zero_tol (1e-12) are treated as zero when the
- * library picks a diagonal, monomial or dense kernel for the matrix. */
+ * library picks a diagonal, monomial or dense kernel for the matrix.
+ * CAST_ERR_ARG for a NULL argument, k out of range, a repeated or
+ * out-of-range qubit or a non-finite entry. */
 cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix);
 
 /* Arithmetic for dense, unitary complex64 gates with k = 4..7 on states of
@@ -359,6 +365,8 @@ cast_status cast_plan_apply(cast_sv *sv, const cast_plan *p);
  * out-pointer may be NULL). */
 cast_status cast_plan_info(const cast_plan *p, int *n_gates, int64_t *total_ops);
 
+/* Free a plan (host memory only; work already queued from it is unaffected).
+ * NULL is accepted. */
 cast_status cast_plan_destroy(cast_plan *p);
 
 /* ------------------------------------------------------------------------
@@ -476,6 +484,8 @@ cast_status cast_adjoint_grad(cast_sv *psi, cast_sv *lam, const cast_circuit *c,
  * mode change rebuilds the graph at the next call. */
 typedef struct cast_hea cast_hea;
 
+/* CAST_ERR_ARG for no instances, a qubit count outside 2..30, layers < 1,
+ * an unknown dtype or a NULL output; CAST_ERR_OOM if the arenas do not fit. */
 cast_status cast_hea_create(int n_instances, const int32_t *n_qubits, int layers, cast_dtype dt,
                             int with_grad, void *cuda_stream, cast_hea **out);
 
@@ -494,6 +504,8 @@ cast_status cast_hea_grad(cast_hea *b, const double *params, double zz, double h
 /* Total parameter count and the largest number of passes per layer. */
 cast_status cast_hea_info(const cast_hea *b, int *n_params, int *n_passes_per_layer_max);
 
+/* Wait for the batch's stream, then free its arenas and graphs.  NULL is
+ * accepted. */
 cast_status cast_hea_destroy(cast_hea *b);
 
 /* ------------------------------------------------------------------------
@@ -517,6 +529,10 @@ cast_status cast_hea_destroy(cast_hea *b);
  * Pauli sums are copied; nothing the caller passed is kept. */
 typedef struct cast_batch cast_batch;
 
+/* CAST_ERR_ARG for no instances, a qubit count outside 1..30, an invalid gate
+ * (qubits, arity, parameter index, non-finite matrix), a negative parameter
+ * offset, an unknown dtype or a NULL output; CAST_ERR_UNSUPPORTED for a gate
+ * of three or more qubits; CAST_ERR_OOM if the arenas do not fit. */
 cast_status cast_batch_create(int n_instances, const cast_circuit *circuits, const int32_t *param_offsets,
                               const cast_pauli_sum *hamiltonians, cast_dtype dt, int with_grad,
                               void *cuda_stream, cast_batch **out);
@@ -531,6 +547,8 @@ cast_status cast_batch_grad(cast_batch *b, const double *params, double *energie
 /* Parameter array length and number of gate steps (the longest gate list). */
 cast_status cast_batch_info(const cast_batch *b, int *n_params, int *n_steps);
 
+/* Free the batch's arenas and graphs (its calls have already waited for
+ * their results).  NULL is accepted. */
 cast_status cast_batch_destroy(cast_batch *b);
 
 /* Thread-local description of the last failure on this host thread. */
