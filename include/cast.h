@@ -113,6 +113,33 @@ cast_status cast_sv_copy_from_host_async(cast_sv *sv, const void *host);
  * out-of-range qubit or a non-finite entry. */
 cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix);
 
+/* Host only (no CUDA call): the kernel family cast_apply_gate takes for this
+ * gate on a state of n_qubits qubits and type dt under the current mode
+ * settings (cast_set_tensor_mode, cast_set_f64_mode,
+ * cast_set_c128_tensor_mode, cast_set_sparse_mode):
+ *   CAST_PATH_DIGIT            complex128 dense-class k = 3..7 as digit
+ *                              products on the tensor cores;
+ *   CAST_PATH_LIST             the sparsity-specialised list kernel (per-row
+ *                              lists of tagged non-zero entries, Section V-A);
+ *   CAST_PATH_TENSOR_CHUNKED   complex64 dense unitary k = 6, 7 on the tensor
+ *                              cores, K fed in chunks;
+ *   CAST_PATH_TENSOR           complex64 dense unitary k = 4, 5 on the tensor
+ *                              cores;
+ *   CAST_PATH_DOUBLE_FLOAT     complex128 k <= 5 in double-float arithmetic
+ *                              on the CUDA cores;
+ *   CAST_PATH_CUDA_CORE        the FP32 / FP64 CUDA-core kernels (identity,
+ *                              diagonal, monomial, dense, cube, tile).
+ * Same arguments and CAST_ERR_ARG cases as cast_apply_gate, plus
+ * n_qubits outside 1..CAST_MAX_QUBITS or an unknown dt. */
+#define CAST_PATH_DIGIT 0
+#define CAST_PATH_LIST 1
+#define CAST_PATH_TENSOR_CHUNKED 2
+#define CAST_PATH_TENSOR 3
+#define CAST_PATH_DOUBLE_FLOAT 4
+#define CAST_PATH_CUDA_CORE 5
+cast_status cast_gate_path(int n_qubits, cast_dtype dt, const int *qubits, int k, const double *matrix,
+                           int *path);
+
 /* Arithmetic for dense, unitary complex64 gates with k = 4..7 on states of
  * at least k + 7 qubits (process-wide setting):
  *   CAST_TC_TF32X3 (default): tcgen05 tensor cores, each operand split into

@@ -389,6 +389,21 @@ def cast_profile_end(capacity=256):
                  bytes=arr[i].bytes, flops=arr[i].flops) for i in range(n.value)]
 
 
+CAST_PATH_DIGIT, CAST_PATH_LIST, CAST_PATH_TENSOR_CHUNKED, CAST_PATH_TENSOR, CAST_PATH_DOUBLE_FLOAT, \
+    CAST_PATH_CUDA_CORE = range(6)
+
+
+def cast_gate_path(n, dtype, qubits, matrix):
+    """The kernel family (CAST_PATH_*) cast_apply_gate takes for this gate on
+    an n-qubit state of the given type under the current modes; host only."""
+    m = np.ascontiguousarray(matrix, dtype=np.complex128)
+    k = len(qubits)
+    q = (ctypes.c_int * k)(*[int(x) for x in qubits])
+    out = ctypes.c_int()
+    _check(load().cast_gate_path(int(n), _dt(dtype), q, k, ctypes.c_void_p(m.ctypes.data), ctypes.byref(out)))
+    return out.value
+
+
 def cast_opcount(matrix, zero_tol=0.0):
     m = np.ascontiguousarray(matrix, dtype=np.complex128)
     k = int(m.shape[0]).bit_length() - 1

@@ -594,14 +594,24 @@ int sm_count_cached() {
     return sms[dev];
 }
 
+int choose_path(const cast_sv *sv, const PreparedGate &g) {
+    if (oz_eligible(sv, g)) return CAST_PATH_DIGIT;
+    if (sparse_preferred(sv, g)) return CAST_PATH_LIST;
+    if (tcc_eligible(sv, g)) return CAST_PATH_TENSOR_CHUNKED;
+    if (tc_eligible(sv, g)) return CAST_PATH_TENSOR;
+    if (df_eligible(sv, g)) return CAST_PATH_DOUBLE_FLOAT;
+    return CAST_PATH_CUDA_CORE;
+}
+
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g) {
-    if (oz_eligible(sv, g)) return launch_gate_oz(sv, g);
-    if (sparse_preferred(sv, g)) return launch_gate_sparse(sv, g);
-    if (tcc_eligible(sv, g)) return launch_gate_tcc(sv, g);
-    if (tc_eligible(sv, g)) return launch_gate_tc(sv, g);
-    if (df_eligible(sv, g)) return launch_gate_df(sv, g);
-    if (sv->dt == CAST_C64) return dispatch<float>(sv, g);
-    return dispatch<double>(sv, g);
+    switch (choose_path(sv, g)) {
+        case CAST_PATH_DIGIT: return launch_gate_oz(sv, g);
+        case CAST_PATH_LIST: return launch_gate_sparse(sv, g);
+        case CAST_PATH_TENSOR_CHUNKED: return launch_gate_tcc(sv, g);
+        case CAST_PATH_TENSOR: return launch_gate_tc(sv, g);
+        case CAST_PATH_DOUBLE_FLOAT: return launch_gate_df(sv, g);
+        default: return sv->dt == CAST_C64 ? dispatch<float>(sv, g) : dispatch<double>(sv, g);
+    }
 }
 
 }  // namespace cast

@@ -351,6 +351,24 @@ static cast_status check_options(const cast_options &o) {
     return CAST_OK;
 }
 
+cast_status cast_gate_path(int n_qubits, cast_dtype dt, const int *qubits, int k, const double *matrix,
+                           int *path) {
+    if (!qubits || !matrix || !path) return fail(CAST_ERR_ARG, "null qubits, matrix or output");
+    if (n_qubits < 1 || n_qubits > CAST_MAX_QUBITS) return fail(CAST_ERR_ARG, "n_qubits out of range");
+    if (dt != CAST_C64 && dt != CAST_C128) return fail(CAST_ERR_ARG, "unknown dtype");
+    if (k < 1 || k > CAST_MAX_K) return fail(CAST_ERR_ARG, "gate size k must be in 1..7");
+    std::vector<cplx> m(size_t(1) << (2 * k));
+    for (size_t i = 0; i < m.size(); i++) m[i] = cplx(matrix[2 * i], matrix[2 * i + 1]);
+    PreparedGate g;
+    cast_status st = prepare_gate(n_qubits, qubits, k, m.data(), 1e-12, &g);
+    if (st != CAST_OK) return st;
+    cast_sv shape;  // only the qubit count and type are read
+    shape.n = n_qubits;
+    shape.dt = dt;
+    *path = choose_path(&shape, g);
+    return CAST_OK;
+}
+
 cast_status cast_apply_gate(cast_sv *sv, const int *qubits, int k, const double *matrix) {
     if (check_sv(sv) != CAST_OK) return CAST_ERR_ARG;
     if (!qubits || !matrix) return fail(CAST_ERR_ARG, "null qubits or matrix");

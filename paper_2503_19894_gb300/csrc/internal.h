@@ -181,6 +181,10 @@ struct SpTile {
 SpTile make_tile_layout(const int *q, int k);
 
 cast_status launch_gate(cast_sv *sv, const PreparedGate &g);
+// The kernel family launch_gate takes for a prepared gate, from the state's
+// qubit count and type and the process-wide mode settings only (host, no
+// CUDA call); values as the CAST_PATH_* constants of cast.h.
+int choose_path(const cast_sv *sv, const PreparedGate &g);
 // Tensor-core path for dense complex64 gates (apply_tc.cu).
 bool tc_eligible(const cast_sv *sv, const PreparedGate &g);
 cast_status launch_gate_tc(cast_sv *sv, const PreparedGate &g);
