@@ -79,6 +79,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "oz_image.h"
 #include "tc.cuh"
 
 namespace cast {
@@ -91,6 +92,7 @@ __device__ int g_oz_error;
 std::atomic<int> g_c128_tc{CAST_C128_TC_OZAKI};
 constexpr uint32_t kOzWait = 1u << 26;
 constexpr int kDigits = 7;
+static_assert(kDigits == kOzImageDigits, "the kernels and the host image agree on the digit count");
 // Measured per 30-qubit gate on a random state (mean of low, high and mixed
 // targets, k = 3 / 4 / 5): 17.6 / 17.3 / 22.6 ms with none of the four
 // options below, 14.7 / 14.6 / 17.6 ms with the first three, 14.2 / 14.1 /
@@ -785,75 +787,6 @@ k_dense_ozc(double2 *__restrict__ sv, uint64_t ntiles, const __grid_constant__ T
 }
 
 // ----------------------------------------------------------------- host side
-// Seven 7-bit digits of |w| / 2^E (49 fractional bits, rounded to nearest,
-// at most 2^49 - 1), E with every |w| of the row below 2^E.
-void host_digits(double w, int E, int *dig) {
-    const double f = std::nearbyint(std::ldexp(std::fabs(w), 49 - E));  // <= 2^49, exact
-    uint64_t F = uint64_t(f);
-    if (F >= (uint64_t(1) << 49)) F = (uint64_t(1) << 49) - 1;
-    for (int j = kDigits - 1; j >= 0; j--) {
-        dig[j] = int(F & 127u);
-        F >>= 7;
-    }
-}
-
-uint16_t host_bf16_digit(int a, int j, bool neg) {
-    if (a == 0) return 0;
-    const float f = std::ldexp(float(a), -7 * j);  // exact: 7 significant bits
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return uint16_t(u >> 16) | (neg ? 0x8000u : 0u);
-}
-
-// The digit image of a gate: W[n][c] (n output real, c input real = 2 member +
-// part) is U's real form; row n gets exponent E_n (every |W[n][c]| < 2^E_n)
-// and its entries' seven digits go to img at off(n, c, j) as bf16 with the
-// sign of the entry; wexp[n] = E_n - 14.
-template <class Off>
-void build_digit_image(const PreparedGate &g, int k, std::vector<uint8_t> &img, int8_t *wexp, Off off, bool unit) {
-    const int D = 1 << k, NR = 2 * D;
-    std::vector<double> W(size_t(NR) * NR);
-    for (int r = 0; r < D; r++)
-        for (int c = 0; c < D; c++) {
-            cplx u = g.m[size_t(r) * D + c];
-            // parts below 2^-100 are dropped (they cannot reach an FP64 output
-            // of a unit-scale row) so every row exponent fits the parameters
-            if (std::fabs(u.real()) < 0x1p-100) u.real(0.0);
-            if (std::fabs(u.imag()) < 0x1p-100) u.imag(0.0);
-            W[size_t(2 * r) * NR + 2 * c] = u.real();
-            W[size_t(2 * r) * NR + 2 * c + 1] = -u.imag();
-            W[size_t(2 * r + 1) * NR + 2 * c] = u.imag();
-            W[size_t(2 * r + 1) * NR + 2 * c + 1] = u.real();
-        }
-    for (int n = 0; n < NR; n++) {
-        int E = -1022;
-        for (int c = 0; c < NR; c++) {
-            const double w = W[size_t(n) * NR + c];
-            if (w != 0.0) {
-                int e;
-                std::frexp(w, &e);  // |w| in [2^(e-1), 2^e)
-                E = std::max(E, e);
-            }
-        }
-        wexp[n] = int8_t(std::max(-128, std::min(127, E - 14)));
-        for (int c = 0; c < NR; c++) {
-            const double w = W[size_t(n) * NR + c];
-            int dig[kDigits];
-            host_digits(w, E, dig);
-            for (int j = 0; j < kDigits; j++) {
-                const uint16_t b = host_bf16_digit(dig[j], unit ? 0 : j, w < 0);
-                std::memcpy(img.data() + off(n, c, j), &b, 2);
-            }
-        }
-    }
-}
-
-// 128-byte swizzled K-major image of rows of 64 bf16: row n (within its 8-row
-// atoms), element c < 64: atom n/8, row n%8, 16-byte chunk (c/8) ^ (n%8)
-inline size_t sw128_bf16(int n, int c) {
-    return size_t(n >> 3) * 1024 + size_t(n & 7) * 128 + size_t(((c >> 3) ^ (n & 7)) << 4) + size_t(c & 7) * 2;
-}
-
 template <int K>
 cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     using S = OzShape<K>;
@@ -861,9 +794,8 @@ cast_status run_oz(cast_sv *sv, const PreparedGate &g) {
     OzParams P{};
     std::vector<uint8_t> img(S::WBYTES, 0);
     // half n / NHW, digit block j, row n % NHW (block 7 stays zero)
-    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
-        return (size_t(n / S::NHW) * S::NACC + size_t(j)) * S::NHW * 128 + sw128_bf16(n % S::NHW, c);
-    }, kOzUnitDigits);
+    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) { return oz_image_offset(n, c, j, S::NHW, S::NACC); },
+                      kOzUnitDigits);
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;
@@ -892,9 +824,9 @@ cast_status run_ozc(cast_sv *sv, const PreparedGate &g) {
     OzcParams P{};
     std::vector<uint8_t> img(size_t(S::NB) * S::WBLK, 0);
     // block (pass n / 64, K-block c / 64): digit j, row n % 64, element c % 64
-    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) {
-        return size_t((n >> 6) * S::NKB + (c >> 6)) * S::WBLK + size_t(j) * S::NHW * 128 + sw128_bf16(n & 63, c & 63);
-    }, false);
+    static_assert(S::NHW == 64, "ozc_image_offset assumes 64-row blocks");
+    build_digit_image(g, K, img, P.wexp, [](int n, int c, int j) { return ozc_image_offset(n, c, j, S::NKB, S::WBLK); },
+                      false);
     const void *dev = nullptr;
     cast_status st = upload_matrix(sv, img.data(), img.size(), &dev);
     if (st != CAST_OK) return st;

@@ -1,4 +1,6 @@
-"""The warp-cube staging tables (csrc/cube.cpp) checked on the host: the C++
+"""Host-built device layouts checked on the host: the warp-cube staging
+tables (csrc/cube.cpp), the list kernel's super-tile and the complex128
+digit images (csrc/oz_image.h).  The warp-cube part: the C++
 check in tests/native/ is compiled against the library's own host source and
 verifies the mapping, the bounds and the bank-conflict bounds for 30000 random
 gates (see the check's header)."""
@@ -46,3 +48,21 @@ def test_sparse_super_tile_layout(tmp_path):
     assert out.returncode == 0, out.stdout + out.stderr
     fields = dict(kv.split("=", 1) for kv in out.stdout.split())
     assert fields["bad"] == "0" and int(fields["checked"]) == 9000
+
+
+def test_digit_images(tmp_path):
+    """The complex128 digit images (csrc/oz_image.h) for k = 3..7 in both
+    layouts: every digit at its own offset, the rest zero, the digits giving
+    back each entry of the real form to 2^(E_n - 49) with its sign
+    (tests/native/oz_image_check.cpp)."""
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path / "oz_image_check")
+    cmd = [gxx, "-O2", "-std=c++17", "-I", CSRC, "-I", "/usr/local/cuda/include",
+           os.path.join(ROOT, "tests", "native", "oz_image_check.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    fields = dict(kv.split("=", 1) for kv in out.stdout.split())
+    assert fields["bad"] == "0" and int(fields["images"]) == 96
